@@ -1,0 +1,640 @@
+/*
+ * FP64 reference ("oracle") for the look-ahead eco-driving DP.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header or table with the CUDA
+ * library.
+ *
+ * What it computes (A GPU Implementation of a Look-Ahead Optimal Controller
+ * for Eco-Driving Based on Dynamic Programming, Zhu et al., ECC 2021):
+ *   - the distance-domain dynamics x_{s+1} = f_s(x_s, u_s) of Eq. (3)-(5) for
+ *     x = [v, soc, t] and u = [T_eng, T_bsg] (plus a brake flag),
+ *   - the stage cost (gamma * mdot_f + 1 - gamma) * dt of Eq. (1), (2), (6),
+ *   - the constraints of Eq. (7) and the traffic-light feasibility of Eq. (8),
+ *   - the backward recursion of Eq. (9a)-(9d) with hard masks (infeasible =
+ *     +inf) instead of the penalty functions phi,
+ *   - a forward rollout that re-minimises at the continuous state.
+ * The loops follow the serial architecture of Sec. IV (Fig. 5): states
+ * (v, soc, t) outermost, then engine torque, motor torque and brake flag, with
+ * the full model evaluated for every state-control pair and no early exits.
+ *
+ * Readings of points the paper leaves open are listed beside the code that
+ * applies them.  Every grid is given per stage as explicit, strictly
+ * increasing node arrays; uniform grids are one case of that.
+ *
+ * FP32-fragile decisions.  A decision whose FP64 outcome is within the FP32
+ * resolution of its threshold (a phase boundary within phase_band seconds, an
+ * acceleration/discriminant/radicand within fp_band of zero, an
+ * interpolation fraction or grid-band edge within fp_band * (1 + scale) index
+ * units of its threshold) is "fragile".  Mode NOMINAL takes every decision
+ * at face value.  Mode LENIENT evaluates every combination of the fragile
+ * decisions of a transition and keeps the smallest cost; mode STRICT keeps
+ * the largest (+inf if any combination is infeasible).  The three modes bound
+ * what a correct lower-precision implementation may return.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_INFEASIBLE 4
+#define ORC_ERR_OOM 2
+
+#define ORC_NOMINAL 0
+#define ORC_LENIENT 1
+#define ORC_STRICT 2
+
+/* Interpolation snapping (reading of the generic DP interpolation the paper
+ * defers to): a fraction below 1e-5 of a cell is snapped to the node, and a
+ * point up to 1e-5 of a cell outside the grid is clamped to the edge. */
+#define SNAP 1e-5
+
+typedef struct {
+    int32_t n_stages;
+    double ds;
+    const double *grade;      /* [n_stages], fraction */
+    /* per-stage grids, stage k = 0..n_stages, node arrays concatenated */
+    const int32_t *nv;
+    const double *v_nodes;
+    const int32_t *nxi;
+    const double *xi_nodes;
+    const int32_t *nt;
+    const double *t_nodes;
+    /* controls */
+    int32_t n_te;
+    const double *te;
+    int32_t n_tm;
+    const double *tm;
+    int32_t n_b;
+    double brake_decel;
+    double a_min, a_max;
+    double mass, cda, crr, rho, g, r_wheel, gear, eta_motor;
+    double voc, r0, cap_As;
+    double fuel_coef[6];
+    double fuel_scale, gamma;
+    double soc_ref, w_soc, v_ref, w_v;
+    int32_t n_lights;
+    const int32_t *light_node;
+    const double *cycle, *red, *offset;
+    double fp_band;    /* relative FP32 resolution band, index units */
+    double phase_band; /* seconds */
+    /* prefix sums of the per-stage sizes: node arrays (N+1 entries each) and
+     * value arrays (N+2 entries, stage k at V_off[k]) */
+    const int64_t *v_off, *xi_off, *t_off, *V_off;
+} orc_problem;
+
+typedef struct {
+    double v1, xi1, t1; /* next state */
+    double dt;          /* driving time of the step, Eq. (2) */
+    double wait;        /* standstill time at a red light before departing */
+    double fuel_rate;   /* g/s while driving */
+    double cost;        /* stage cost, Eq. (6) */
+} orc_trans;
+
+/* Decision bookkeeping for FP32-fragile comparisons. */
+typedef struct {
+    uint32_t mask; /* which fragile decisions to flip */
+    int nf;        /* fragile decisions met so far */
+} dec_ctx;
+
+static int decide(dec_ctx *d, int nominal, int fragile)
+{
+    if (!fragile || d == NULL)
+        return nominal;
+    int flip = (d->nf < 31) ? (int)((d->mask >> d->nf) & 1u) : 0;
+    d->nf++;
+    return nominal ^ flip;
+}
+
+/* ---- grids --------------------------------------------------------------- */
+
+static int64_t value_offset(const orc_problem *P, int stage) { return P->V_off[stage]; }
+
+int64_t orc_value_offset(const orc_problem *P, int stage) { return value_offset(P, stage); }
+
+/* ---- traffic lights (Fig. 3, Eq. 5c, Eq. 8) ------------------------------ */
+
+static int light_at(const orc_problem *P, int node)
+{
+    for (int j = 0; j < P->n_lights; ++j)
+        if (P->light_node[j] == node)
+            return j;
+    return -1;
+}
+
+/* Position inside the light cycle: ((t - offset) mod cycle) in [0, cycle).
+ * Reading: red comes first after the offset and lasts red[j] seconds. */
+static double phase_of(const orc_problem *P, int j, double t)
+{
+    double c = P->cycle[j];
+    double ph = fmod(t - P->offset[j], c);
+    if (ph < 0)
+        ph += c;
+    if (ph >= c)
+        ph -= c;
+    return ph;
+}
+
+int orc_is_red(const orc_problem *P, int j, double t)
+{
+    return phase_of(P, j, t) < P->red[j];
+}
+
+static int phase_fragile(const orc_problem *P, int j, double ph)
+{
+    double b = P->phase_band;
+    return ph < b || fabs(ph - P->red[j]) < b || P->cycle[j] - ph < b;
+}
+
+/* ---- model: one distance step (Eq. 2, 5a-5c, 7) ---------------------------
+ * Readings: P0 drivetrain with one total ratio gear/r_wheel; engine and motor
+ * speeds are v * gear / r_wheel taken at the stage-start speed (the powertrain
+ * model takes the current speed, Sec. IV); constant motor efficiency; battery
+ * as a zeroth-order circuit, I = (Voc - sqrt(Voc^2 - 4 R0 P)) / (2 R0); no
+ * auxiliary load.  Stopping: if v^2 + 2 ds a < 0 the step is infeasible,
+ * except when the next node holds a light, where the vehicle stops at the
+ * stop line (v' = 0, dt = 2 ds / v).  Red arrival: arriving at a light node
+ * with v' > 0 while it is red is infeasible.  Departure: standing (v = 0) at
+ * a light node while red, the vehicle waits for green, at a time-only cost
+ * (1 - gamma) * wait and with the engine off.  Returns 1 when feasible. */
+static int transition(const orc_problem *P, int k, double v, double xi, double t,
+                      double Te, double Tm, int b, dec_ctx *d, orc_trans *o)
+{
+    const double M = P->mass;
+    double p = P->grade[k];
+    double sq = sqrt(1.0 + p * p);
+    double sin_th = p / sq, cos_th = 1.0 / sq;
+    double F_road = M * P->g * (P->crr * cos_th + sin_th) + 0.5 * P->rho * P->cda * v * v;
+    double ratio = P->gear / P->r_wheel;
+    double F_tr = (Te + Tm) * ratio - (b ? M * P->brake_decel : 0.0);
+    double a = (F_tr - F_road) / M;
+    double ea = P->fp_band * (fabs(F_tr) + fabs(F_road)) / M;
+
+    /* Eq. (7d): comfort acceleration limits */
+    if (decide(d, a < P->a_min, fabs(a - P->a_min) <= ea))
+        return 0;
+    if (decide(d, a > P->a_max, fabs(a - P->a_max) <= ea))
+        return 0;
+
+    /* waiting for green when standing at a light node */
+    double wait = 0.0;
+    int lk = light_at(P, k);
+    if (lk >= 0 && v == 0.0) {
+        double ph = phase_of(P, lk, t);
+        int red = ph < P->red[lk];
+        if (decide(d, red, phase_fragile(P, lk, ph))) {
+            if (ph < P->red[lk])
+                wait = P->red[lk] - ph;
+            else if (ph > 0.5 * (P->red[lk] + P->cycle[lk]))
+                wait = P->red[lk] + (P->cycle[lk] - ph); /* red is about to start */
+            else
+                wait = 0.0; /* green has just started */
+        }
+    }
+
+    /* Eq. (5a) and Eq. (2) */
+    double R = v * v + 2.0 * P->ds * a;
+    double eR = P->fp_band * (v * v + 2.0 * P->ds * fabs(a));
+    int next_light = light_at(P, k + 1);
+    double v1, dt;
+    if (decide(d, R < 0.0, fabs(R) <= eR)) {
+        if (next_light >= 0 && v > 0.0) {
+            v1 = 0.0;
+            dt = 2.0 * P->ds / v;
+        } else {
+            return 0;
+        }
+    } else {
+        v1 = sqrt(R > 0.0 ? R : 0.0);
+        if (v + v1 <= 0.0)
+            return 0;
+        dt = 2.0 * P->ds / (v + v1);
+    }
+    double t1 = t + wait + dt;
+
+    /* Eq. (5c), (7c), (8): no arrival at a light node during red unless
+     * stopped at the line; evaluated at the continuous arrival time. */
+    if (next_light >= 0 && v1 > 0.0) {
+        double ph = phase_of(P, next_light, t1);
+        if (decide(d, ph < P->red[next_light], phase_fragile(P, next_light, ph)))
+            return 0;
+    }
+
+    /* powertrain: fuel map and BSG power */
+    double w = v * ratio;
+    double mf = 0.0;
+    if (Te > 0.0) {
+        const double *c = P->fuel_coef;
+        mf = P->fuel_scale * (c[0] + c[1] * w + c[2] * Te + c[3] * w * Te + c[4] * w * w + c[5] * Te * Te);
+    }
+    double Pm = Tm * w;
+    double Pb = Pm > 0.0 ? Pm / P->eta_motor : Pm * P->eta_motor;
+
+    /* Eq. (5b): zeroth-order battery; infeasible if the power exceeds what
+     * the circuit can deliver (negative discriminant). */
+    double disc = P->voc * P->voc - 4.0 * P->r0 * Pb;
+    double ed = P->fp_band * (P->voc * P->voc + 4.0 * P->r0 * fabs(Pb));
+    if (decide(d, disc < 0.0, fabs(disc) <= ed))
+        return 0;
+    if (disc < 0.0)
+        disc = 0.0;
+    double I = (P->voc - sqrt(disc)) / (2.0 * P->r0);
+    double dxi = dt * I / P->cap_As;
+
+    o->v1 = v1;
+    o->xi1 = xi - dxi;
+    o->t1 = t1;
+    o->dt = dt;
+    o->wait = wait;
+    o->fuel_rate = mf;
+    /* Eq. (1)/(6): weighted fuel and time; waiting costs time only */
+    o->cost = (P->gamma * mf + 1.0 - P->gamma) * dt + (1.0 - P->gamma) * wait;
+    return 1;
+}
+
+/* ---- interpolation on a stage grid ---------------------------------------- */
+
+/* Locate x on an increasing node array.  Returns 0 when x lies outside the
+ * grid by more than SNAP of the end cell.  scale sets the FP32 band. */
+static int locate(const double *nodes, int n, double x, double scale, double fp_band,
+                  dec_ctx *d, int *i0, double *f)
+{
+    if (n == 1) {
+        if (fabs(x - nodes[0]) <= 1e-12 * (1.0 + fabs(nodes[0]))) {
+            *i0 = 0;
+            *f = 0.0;
+            return 1;
+        }
+        return 0;
+    }
+    double lo = nodes[0], hi = nodes[n - 1];
+    double h0 = nodes[1] - nodes[0], h1 = nodes[n - 1] - nodes[n - 2];
+    double eps = fp_band * (1.0 + fabs(scale));
+    double below = (lo - x) / h0, above = (x - hi) / h1;
+    if (decide(d, below > SNAP, fabs(below - SNAP) <= eps))
+        return 0;
+    if (decide(d, above > SNAP, fabs(above - SNAP) <= eps))
+        return 0;
+    if (x < lo)
+        x = lo;
+    if (x > hi)
+        x = hi;
+    int a = 0, b = n - 1; /* invariant nodes[a] <= x, and x < nodes[b] or b = n-1 */
+    while (b - a > 1) {
+        int m = (a + b) / 2;
+        if (nodes[m] <= x)
+            a = m;
+        else
+            b = m;
+    }
+    int i = a < n - 1 ? a : n - 2;
+    double ff = (x - nodes[i]) / (nodes[i + 1] - nodes[i]);
+    if (decide(d, ff < SNAP, fabs(ff - SNAP) <= eps))
+        ff = 0.0;
+    else if (decide(d, ff > 1.0 - SNAP, fabs(ff - (1.0 - SNAP)) <= eps))
+        ff = 1.0;
+    *i0 = i;
+    *f = ff;
+    return 1;
+}
+
+/* Trilinear interpolation of a stage value array; corners with weight
+ * exactly 0 are skipped and any other +inf corner makes the result +inf. */
+static double interp3(const orc_problem *P, int stage, const double *V, double v, double xi, double t,
+                      const double scale[3], dec_ctx *d)
+{
+    int nv = P->nv[stage], nx = P->nxi[stage], nt = P->nt[stage];
+    const double *vn = P->v_nodes + P->v_off[stage];
+    const double *xn = P->xi_nodes + P->xi_off[stage];
+    const double *tn = P->t_nodes + P->t_off[stage];
+    int iv, ix, it;
+    double fv, fx, ft;
+    if (!locate(vn, nv, v, scale[0], P->fp_band, d, &iv, &fv))
+        return INFINITY;
+    if (!locate(xn, nx, xi, scale[1], P->fp_band, d, &ix, &fx))
+        return INFINITY;
+    if (!locate(tn, nt, t, scale[2], P->fp_band, d, &it, &ft))
+        return INFINITY;
+    double acc = 0.0;
+    for (int a = 0; a < 2; ++a) {
+        double wa = a ? fv : 1.0 - fv;
+        if (wa == 0.0)
+            continue;
+        for (int b = 0; b < 2; ++b) {
+            double wb = b ? fx : 1.0 - fx;
+            if (wb == 0.0)
+                continue;
+            for (int c = 0; c < 2; ++c) {
+                double wc = c ? ft : 1.0 - ft;
+                if (wc == 0.0)
+                    continue;
+                double val = V[((int64_t)(iv + a) * nx + (ix + b)) * nt + (it + c)];
+                if (isinf(val))
+                    return INFINITY;
+                acc += wa * wb * wc * val;
+            }
+        }
+    }
+    return acc;
+}
+
+/* Terminal cost c_T (Eq. 9a; reading: SoC shortfall and speed deviation). */
+double orc_terminal_cost(const orc_problem *P, double v, double xi)
+{
+    double short_soc = P->soc_ref - xi;
+    if (short_soc < 0.0)
+        short_soc = 0.0;
+    return P->w_soc * short_soc + P->w_v * (v - P->v_ref) * (v - P->v_ref);
+}
+
+/* One transition's cost-to-go term c + J_{k+1}(f(x, u)) under a decision
+ * mask.  abs_scale: use absolute grid positions for the FP32 bands (states
+ * off the grid, as in the rollout) instead of the step's shift. */
+static double eval_once(const orc_problem *P, int k, const double *Vnext, double v, double xi, double t,
+                        int ie, int im, int b, int abs_scale, dec_ctx *d, orc_trans *tr)
+{
+    if (!transition(P, k, v, xi, t, P->te[ie], P->tm[im], b, d, tr))
+        return INFINITY;
+    int s1 = k + 1;
+    const double *vn = P->v_nodes + P->v_off[s1];
+    const double *xn = P->xi_nodes + P->xi_off[s1];
+    const double *tn = P->t_nodes + P->t_off[s1];
+    int nv = P->nv[s1], nx = P->nxi[s1], nt = P->nt[s1];
+    double hv = nv > 1 ? (vn[nv - 1] - vn[0]) / (nv - 1) : 1.0;
+    double hx = nx > 1 ? (xn[nx - 1] - xn[0]) / (nx - 1) : 1.0;
+    double ht = nt > 1 ? (tn[nt - 1] - tn[0]) / (nt - 1) : 1.0;
+    double scale[3];
+    scale[0] = (tr->v1 - vn[0]) / hv;
+    if (abs_scale || tr->wait > 0.0) {
+        scale[1] = (tr->xi1 - xn[0]) / hx;
+        scale[2] = (tr->t1 - tn[0]) / ht;
+    } else {
+        scale[1] = (tr->xi1 - xi) / hx;
+        scale[2] = (tr->t1 - t) / ht;
+    }
+    double J = interp3(P, s1, Vnext, tr->v1, tr->xi1, tr->t1, scale, d);
+    if (isinf(J))
+        return INFINITY;
+    return tr->cost + J;
+}
+
+/* Evaluate a transition in the given mode; *nfrag returns how many fragile
+ * decisions the nominal evaluation met. */
+static double eval_mode(const orc_problem *P, int k, const double *Vnext, double v, double xi, double t,
+                        int ie, int im, int b, int mode, int abs_scale, int *nfrag, orc_trans *tr_nom)
+{
+    dec_ctx d = {0u, 0};
+    orc_trans tr;
+    memset(&tr, 0, sizeof tr);
+    double F0 = eval_once(P, k, Vnext, v, xi, t, ie, im, b, abs_scale, &d, &tr);
+    if (tr_nom)
+        *tr_nom = tr;
+    if (nfrag)
+        *nfrag = d.nf;
+    if (mode == ORC_NOMINAL || d.nf == 0)
+        return F0;
+    int m = d.nf;
+    double lo = F0, hi = F0;
+    for (uint32_t mask = 1; mask < (1u << (m < 10 ? m : 10)); ++mask) {
+        dec_ctx dd = {mask, 0};
+        orc_trans t2;
+        double F = eval_once(P, k, Vnext, v, xi, t, ie, im, b, abs_scale, &dd, &t2);
+        if (dd.nf > m && dd.nf <= 10)
+            m = dd.nf; /* a flipped branch met further fragile decisions */
+        if (F < lo)
+            lo = F;
+        if (F > hi || isinf(F))
+            hi = F;
+    }
+    if (m > 10)
+        hi = INFINITY;
+    return mode == ORC_LENIENT ? lo : hi;
+}
+
+/* ---- public entry points ---------------------------------------------------- */
+
+/* One model step, for unit tests: out = {v1, xi1, t1, dt, wait, fuel_rate,
+ * cost}; returns 1 if feasible (nominal decisions). */
+int orc_model_step(const orc_problem *P, int k, double v, double xi, double t, double Te, double Tm,
+                   int b, double *out)
+{
+    orc_trans tr;
+    memset(&tr, 0, sizeof tr);
+    int ok = transition(P, k, v, xi, t, Te, Tm, b, NULL, &tr);
+    out[0] = tr.v1;
+    out[1] = tr.xi1;
+    out[2] = tr.t1;
+    out[3] = tr.dt;
+    out[4] = tr.wait;
+    out[5] = tr.fuel_rate;
+    out[6] = tr.cost;
+    return ok;
+}
+
+/* Interpolate a stage value array at a point (nominal decisions). */
+double orc_interp(const orc_problem *P, int stage, const double *V, double v, double xi, double t)
+{
+    double scale[3] = {0.0, 0.0, 0.0};
+    return interp3(P, stage, V, v, xi, t, scale, NULL);
+}
+
+/* Terminal values J_N = c_T on the last stage grid (Eq. 9a). */
+int orc_terminal(const orc_problem *P, double *VN)
+{
+    int s = P->n_stages;
+    const double *vn = P->v_nodes + P->v_off[s];
+    const double *xn = P->xi_nodes + P->xi_off[s];
+    int nv = P->nv[s], nx = P->nxi[s], nt = P->nt[s];
+    for (int i = 0; i < nv; ++i)
+        for (int j = 0; j < nx; ++j)
+            for (int l = 0; l < nt; ++l)
+                VN[((int64_t)i * nx + j) * nt + l] = orc_terminal_cost(P, vn[i], xn[j]);
+    return ORC_OK;
+}
+
+/* One backward step of Eq. (9b)-(9d) at stage k.
+ *   Vnext: J_{k+1} on the stage-(k+1) grid.
+ *   idx:   NULL for every state of stage k (outputs hold nv*nxi*nt entries,
+ *          t fastest), or n_idx flat state indices (outputs hold n_idx).
+ *   Vout:  J_k (mode-dependent, +inf when infeasible).
+ *   pi:    argmin control u = (ie * n_tm + im) * n_b + b, lowest u on ties,
+ *          -1 when infeasible (may be NULL).
+ *   second: the second-smallest transition value over distinct controls
+ *          (may be NULL).
+ *   nfrag: number of controls whose evaluation met a fragile decision (may
+ *          be NULL).
+ */
+int orc_stage(const orc_problem *P, int k, int mode, const double *Vnext, int64_t n_idx, const int64_t *idx,
+              double *Vout, int32_t *pi, double *second, int32_t *nfrag, int nthreads)
+{
+    if (k < 0 || k >= P->n_stages || !Vnext || !Vout)
+        return ORC_ERR_ARG;
+    int nv = P->nv[k], nx = P->nxi[k], nt = P->nt[k];
+    const double *vn = P->v_nodes + P->v_off[k];
+    const double *xn = P->xi_nodes + P->xi_off[k];
+    const double *tn = P->t_nodes + P->t_off[k];
+    int64_t total = idx ? n_idx : (int64_t)nv * nx * nt;
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t q = 0; q < total; ++q) {
+        int64_t s = idx ? idx[q] : q;
+        int i = (int)(s / ((int64_t)nx * nt));
+        int j = (int)((s / nt) % nx);
+        int l = (int)(s % nt);
+        double v = vn[i], xi = xn[j], t = tn[l];
+        double best = INFINITY, sec = INFINITY;
+        int32_t bu = -1, nf_total = 0;
+        /* Fig. 5: engine torque, motor torque, brake flag innermost */
+        for (int ie = 0; ie < P->n_te; ++ie)
+            for (int im = 0; im < P->n_tm; ++im)
+                for (int b = 0; b < P->n_b; ++b) {
+                    int nf = 0;
+                    double F = eval_mode(P, k, Vnext, v, xi, t, ie, im, b, mode, 0, &nf, NULL);
+                    nf_total += nf > 0;
+                    if (F < best) {
+                        sec = best;
+                        best = F;
+                        bu = (ie * P->n_tm + im) * P->n_b + b;
+                    } else if (F < sec) {
+                        sec = F;
+                    }
+                }
+        Vout[q] = best;
+        if (pi)
+            pi[q] = isinf(best) ? -1 : bu;
+        if (second)
+            second[q] = sec;
+        if (nfrag)
+            nfrag[q] = nf_total;
+    }
+    return ORC_OK;
+}
+
+/* Full backward sweep in one mode: Vall holds J_0..J_N back to back (stage
+ * k at orc_value_offset(k)), piall holds pi_0..pi_{N-1} with the same
+ * offsets (may be NULL), secall likewise (may be NULL). */
+int orc_solve(const orc_problem *P, int mode, double *Vall, int32_t *piall, double *secall, int nthreads)
+{
+    int N = P->n_stages;
+    orc_terminal(P, Vall + value_offset(P, N));
+    for (int k = N - 1; k >= 0; --k) {
+        int64_t o = value_offset(P, k);
+        int rc = orc_stage(P, k, mode, Vall + value_offset(P, k + 1), 0, NULL, Vall + o,
+                           piall ? piall + o : NULL, secall ? secall + o : NULL, NULL, nthreads);
+        if (rc)
+            return rc;
+    }
+    return ORC_OK;
+}
+
+/* Forward rollout from x0 through J_1..J_N (Vall as in orc_solve): at every
+ * stage re-minimise c + J_{k+1}(f(x, u)) over all controls at the continuous
+ * state, apply the argmin (lowest u on ties) and accumulate.
+ *   traj:  [(N+1) * 3] states (v, soc, t)
+ *   u:     [N] controls; step: [N * 5] (dt, wait, fuel_g, cost, gap) where gap
+ *          is (second - best) / |best| of that stage's minimisation
+ *   totals: fuel_g, time_s, J (sum of stage costs + c_T(x_N))
+ * Returns ORC_ERR_INFEASIBLE (and the stage in totals[3]) if no control is
+ * feasible somewhere along the way. */
+int orc_rollout(const orc_problem *P, const double *Vall, const double *x0, double *traj, int32_t *u,
+                double *step, double *totals)
+{
+    int N = P->n_stages;
+    double v = x0[0], xi = x0[1], t = x0[2];
+    double fuel = 0.0, J = 0.0;
+    traj[0] = v;
+    traj[1] = xi;
+    traj[2] = t;
+    for (int k = 0; k < N; ++k) {
+        const double *Vn = Vall + value_offset(P, k + 1);
+        double best = INFINITY, sec = INFINITY;
+        int bu = -1;
+        orc_trans bt;
+        memset(&bt, 0, sizeof bt);
+        for (int ie = 0; ie < P->n_te; ++ie)
+            for (int im = 0; im < P->n_tm; ++im)
+                for (int b = 0; b < P->n_b; ++b) {
+                    orc_trans tr;
+                    double F = eval_mode(P, k, Vn, v, xi, t, ie, im, b, ORC_NOMINAL, 1, NULL, &tr);
+                    if (F < best) {
+                        sec = best;
+                        best = F;
+                        bu = (ie * P->n_tm + im) * P->n_b + b;
+                        bt = tr;
+                    } else if (F < sec) {
+                        sec = F;
+                    }
+                }
+        if (bu < 0) {
+            totals[0] = fuel;
+            totals[1] = t - x0[2];
+            totals[2] = INFINITY;
+            totals[3] = k;
+            return ORC_ERR_INFEASIBLE;
+        }
+        u[k] = bu;
+        double fuel_k = bt.fuel_rate * bt.dt;
+        step[k * 5 + 0] = bt.dt;
+        step[k * 5 + 1] = bt.wait;
+        step[k * 5 + 2] = fuel_k;
+        step[k * 5 + 3] = bt.cost;
+        step[k * 5 + 4] = isinf(sec) ? INFINITY : (sec - best) / fabs(best);
+        fuel += fuel_k;
+        J += bt.cost;
+        v = bt.v1;
+        xi = bt.xi1;
+        t = bt.t1;
+        traj[(k + 1) * 3 + 0] = v;
+        traj[(k + 1) * 3 + 1] = xi;
+        traj[(k + 1) * 3 + 2] = t;
+    }
+    J += orc_terminal_cost(P, v, xi);
+    totals[0] = fuel;
+    totals[1] = t - x0[2];
+    totals[2] = J;
+    totals[3] = -1;
+    return ORC_OK;
+}
+
+/* Cost of a given control sequence from x0 (exact model, no grid): the
+ * brute-force pin enumerates sequences with this.  Returns +inf if any step
+ * is infeasible or leaves the state box [lo, hi] of the given stage grid. */
+double orc_sequence_cost(const orc_problem *P, const double *x0, const int32_t *useq, double *xN)
+{
+    double v = x0[0], xi = x0[1], t = x0[2], J = 0.0;
+    for (int k = 0; k < P->n_stages; ++k) {
+        int u = useq[k];
+        int b = u % P->n_b;
+        int im = (u / P->n_b) % P->n_tm;
+        int ie = u / (P->n_b * P->n_tm);
+        orc_trans tr;
+        if (!transition(P, k, v, xi, t, P->te[ie], P->tm[im], b, NULL, &tr))
+            return INFINITY;
+        int s1 = k + 1;
+        const double *vn = P->v_nodes + P->v_off[s1];
+        const double *xn = P->xi_nodes + P->xi_off[s1];
+        const double *tn = P->t_nodes + P->t_off[s1];
+        if (tr.v1 < vn[0] || tr.v1 > vn[P->nv[s1] - 1] || tr.xi1 < xn[0] || tr.xi1 > xn[P->nxi[s1] - 1] ||
+            tr.t1 < tn[0] || tr.t1 > tn[P->nt[s1] - 1])
+            return INFINITY;
+        J += tr.cost;
+        v = tr.v1;
+        xi = tr.xi1;
+        t = tr.t1;
+    }
+    if (xN) {
+        xN[0] = v;
+        xN[1] = xi;
+        xN[2] = t;
+    }
+    return J + orc_terminal_cost(P, v, xi);
+}
