@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: paper-scale eco-driving DP horizon solve on GB300.
+
+One step = one pass of the whole hot path on the paper-scale instance
+(1000 m horizon of 100 steps of 10 m; 51 speeds x 51 SoC x 201 times;
+31 x 31 torques x brake flag = 1922 controls; 4 lights): terminal values, per
+stage the precompute and Bellman kernels (the backward recursion of Eq. 9),
+then the forward rollout.  The metric is state x control evaluations per
+second counted as the paper counts them (N * states * controls per solve),
+with ms per horizon solve beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference implementation of this method is
+that oracle; the paper ships no code).  With --gpus N > 1 (under torchrun)
+every rank solves its own replica of the instance (independent problems, no
+collective on the data path) and the value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DP state x control evals/s (ms per horizon solve)"
+UNIT = "evals/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum per Bellman launch from an ncu
+# capture of the current kernel (None until captured for this kernel version).
+BELLMAN_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload(seed):
+    from paper_2104_01284_gb300 import problems as P
+    return P.config1(seed=seed)
+
+
+def config_dict(p, n_gpus, flush):
+    return {"workload": f"paper-scale horizon: {p.n_stages} stages x {p.n_v}x{p.n_soc}x{p.n_t} states x "
+                        f"{p.n_controls} controls, {len(p.light_stage)} lights (seed 1)",
+            "n_stages": p.n_stages, "grid": [p.n_v, p.n_soc, p.n_t], "controls": p.n_controls,
+            "evals_per_solve": p.evals_per_solve, "parallelism": f"replicas x{n_gpus}", "l2": flush}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(p, target_s, seed=11):
+    """Time the FP64 oracle (as it stands) on the host cores on a bounded
+    sample: one Bellman stage of the same instance evaluated at a seeded
+    random subset of states, every control at each."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2104_01284_gb300 import problems as P
+    op = O.make(p)
+    k = p.n_stages // 2
+    Vn = P.synthetic_value_field(p, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    probe = rng.choice(p.n_states, size=2000, replace=False)
+    t0 = time.perf_counter()
+    O.stage(op, k, Vn, idx=probe)
+    rate = probe.size / max(1e-6, time.perf_counter() - t0)
+    n = int(min(p.n_states, max(2000, rate * target_s)))
+    idx = rng.choice(p.n_states, size=n, replace=False)
+    t0 = time.perf_counter()
+    O.stage(op, k, Vn, idx=idx)
+    dt = time.perf_counter() - t0
+    evals = n * p.n_controls
+    return {"value": evals / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one Bellman stage (k={k}) of the bench instance at {n} random states x "
+                      f"{p.n_controls} controls = {evals:.3e} evals in {dt:.1f} s, FP64, OpenMP"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_2104_01284_gb300 import problems as P
+    p = workload(args.seed)
+    op = O.make(p)
+    k = p.n_stages // 2
+    Vn = P.synthetic_value_field(p, seed=11)
+    rng = np.random.Generator(np.random.PCG64(12))
+    probe = rng.choice(p.n_states, size=1000, replace=False)
+    t0 = time.perf_counter()
+    O.stage(op, k, Vn, idx=probe)
+    rate = probe.size / max(1e-6, time.perf_counter() - t0)
+    # every step a bounded sample: about 120 s for the whole run
+    per_step_s = max(0.5, min(5.0, 120.0 / max(1, args.steps + args.warmup)))
+    n = int(min(p.n_states, max(500, rate * per_step_s)))
+    for _ in range(args.warmup):
+        O.stage(op, k, Vn, idx=rng.choice(p.n_states, size=n, replace=False))
+    times = []
+    for _ in range(args.steps):
+        idx = rng.choice(p.n_states, size=n, replace=False)
+        t0 = time.perf_counter()
+        O.stage(op, k, Vn, idx=idx)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    evals = n * p.n_controls * args.steps
+    value = evals / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "ms_per_solve_equiv": 1e3 * p.evals_per_solve / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": config_dict(p, args.gpus, "CPU run"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"per step one Bellman stage (k={k}) at {n} random states x {p.n_controls} "
+                                   f"controls, FP64, OpenMP"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2104_01284_gb300.solver import EcoDP
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = workload(args.seed)
+    stream = torch.cuda.Stream(dev)
+    dp = EcoDP(p, device=dev, stream=stream)
+    launches_per_step = 1 + 2 * p.n_stages + 1  # terminal, N x (precompute, Bellman), rollout
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            dp.solve(stream)
+            dp.rollout(stream=stream)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)  # evict the previous step's data from L2 (outside the timed pair)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dp.solve(stream)
+            traj = dp.rollout(stream=stream)
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * p.evals_per_solve * args.steps / (total_ms / 1e3)
+
+    # per-kernel breakdown (direct launches, CUDA events on the launching stream)
+    profs = [dp.profile_sweep(stream) for _ in range(3)]
+    stats = dp.sweep_stats(stream)
+    bell_ms = statistics.median(x["bellman"] for x in profs)
+    pre_ms = statistics.median(x["precompute"] for x in profs)
+    sweep_ms = statistics.median(x["sweep"] for x in profs)
+    per_launch_s = bell_ms / 1e3 / p.n_stages
+    flops_per_launch = 4.0 * stats["effective_evals"] / p.n_stages  # 2 FMA per feasible state x control
+    achieved = flops_per_launch / per_launch_s / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "bellman_tiled", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": BELLMAN_TRAFFIC_BYTES,
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts)",
+                "work_basis": "4 FLOP (2 FMA) per effective state x control evaluation",
+                "bellman_ms_per_launch": 1e3 * per_launch_s,
+                "share_of_sweep": bell_ms / sweep_ms if sweep_ms > 0 else None,
+                "precompute_ms_per_launch": pre_ms / p.n_stages,
+                "effective_evals_per_s": stats["effective_evals"] / (bell_ms / 1e3)}
+
+    # end to end through the public API with host buffers: upload the
+    # problem tables, solve, read the trajectory back, every step
+    for _ in range(2):
+        dp.update(p, stream)
+        dp.solve(stream)
+        dp.rollout(stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dp.update(p, stream)
+        dp.solve(stream)
+        dp.rollout(stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * p.evals_per_solve * args.steps / float(te.item()), "unit": UNIT,
+           "h2d_bytes_per_step": int(stats["h2d_update_bytes"]), "d2h_bytes_per_step": int(stats["d2h_rollout_bytes"]),
+           "ms_per_step": 1e3 * float(te.item()) / args.steps}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": config_dict(p, world, "flushed between steps (256 MB write)"),
+        "effective_evals_per_s": world * stats["effective_evals"] * args.steps / (total_ms / 1e3),
+        "rollout": {"fuel_g": traj["fuel_g"], "time_s": traj["time_s"], "J": traj["J"]},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dp.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * ecodp.h -- C ABI of the GB300 dynamic-programming solver for look-ahead
+ * eco-driving (Zhu, Gupta, Pivaro, Deshpande, Canova: "A GPU Implementation
+ * of a Look-Ahead Optimal Controller for Eco-Driving Based on Dynamic
+ * Programming", ECC 2021).
+ *
+ * The solver computes, on one GPU and in FP32, the backward recursion of
+ * Eq. (9a)-(9d) over the three-state grid x = [v, SoC, t] (Eq. 4a) with
+ * controls u = [T_eng, T_bsg] plus a brake flag (Eq. 4b), the dynamics of
+ * Eq. (5a)-(5c), the stage cost of Eq. (1)/(6) and the constraints of
+ * Eq. (7)/(8), followed by a forward rollout that extracts the optimal
+ * speed/SoC/time trajectory.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a dp_status; none aborts, exits or prints.  The
+ *     message of the last failure on the calling thread is dp_last_error().
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that take a stream enqueue their GPU work on it and
+ *     return before it finishes unless they copy results to host memory.
+ *   - Arrays are C order.  Value arrays are float32 [n_v][n_soc][n_t] (t
+ *     fastest); infeasible states hold +INFINITY.  Policies are int16 of the
+ *     same shape holding the control index u = (i_eng * n_tm + i_bsg) *
+ *     n_brake + brake, or -1 where the state is infeasible.
+ *   - A problem object owns all its device memory (allocated through the
+ *     caller's allocator when one is given) and frees it in
+ *     dp_problem_destroy.  The caller owns descriptors and output buffers.
+ *   - After DP_ERR_CUDA the problem object must only be destroyed.
+ */
+#ifndef ECODP_H
+#define ECODP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DP_OK = 0,
+    DP_ERR_INVALID_ARG = 1, /* a descriptor field or argument is out of range */
+    DP_ERR_OOM = 2,         /* the allocator returned NULL */
+    DP_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    DP_ERR_INFEASIBLE = 4,  /* no feasible control at some rollout stage */
+    DP_ERR_NOT_SOLVED = 5,  /* results requested before dp_solve_backward */
+    DP_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+    DP_ERR_INTERNAL = 7     /* a kernel reported an inconsistency */
+} dp_status;
+
+/* Device-memory allocator supplied by the caller (for example a wrapper of
+ * PyTorch's caching allocator).  alloc returns a device pointer or NULL;
+ * free releases it.  Both are called on the creating thread, with the
+ * stream given to dp_problem_create.  A NULL allocator makes the library use
+ * cudaMallocAsync / cudaFreeAsync on that stream. */
+typedef struct dp_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} dp_allocator;
+
+/* One receding-horizon problem (Eq. 6) in SI units.  All grids are uniform
+ * with inclusive ends: node i of an n-point grid over [lo, hi] is
+ * lo + (hi - lo) * i / (n - 1).  Copied at create/update; the caller keeps
+ * ownership of the arrays. */
+typedef struct dp_problem_desc {
+    int32_t n_stages;     /* N distance steps of ds metres (Eq. 1) */
+    double ds;            /* distance step Delta d, m (Eq. 2) */
+    const double *grade;  /* [n_stages] road grade per step, fraction (Eq. 5a) */
+    double v_lo, v_hi;    /* speed grid, m/s; its ends are the limits of Eq. 7a */
+    int32_t n_v;          /* >= 2 */
+    double soc_lo, soc_hi; /* SoC grid, fraction; limits of Eq. 7b */
+    int32_t n_soc;        /* >= 2 */
+    double t_lo, t_hi;    /* time grid, s; t_hi is the horizon's t_f (Eq. 8) */
+    int32_t n_t;          /* >= 2 */
+    double te_lo, te_hi;  /* engine torque grid, Nm (Eq. 7e); te_lo >= 0 */
+    int32_t n_te;         /* >= 1 */
+    double tm_lo, tm_hi;  /* BSG torque grid, Nm (Eq. 7f) */
+    int32_t n_tm;         /* >= 1 */
+    int32_t n_brake;      /* 1 = no brake control, 2 = brake flag {0, 1} */
+    double brake_decel;   /* deceleration added by the brake flag, m/s^2 */
+    double a_min, a_max;  /* comfort acceleration limits, m/s^2 (Eq. 7d) */
+    double mass, cda, crr, rho, g; /* road load (Eq. 5a) */
+    double r_wheel, gear;          /* one total ratio gear / r_wheel, 1/m */
+    double eta_motor;              /* constant BSG efficiency in (0, 1] */
+    double voc, r0, capacity_As;   /* zeroth-order battery (Eq. 5b) */
+    double fuel_coef[6];  /* mdot = s (c0 + c1 w + c2 T + c3 w T + c4 w^2 + c5 T^2) g/s, T > 0 */
+    double fuel_scale;    /* s */
+    double gamma;         /* fuel/time weight of Eq. 1 in [0, 1] */
+    double soc_ref, w_soc, v_ref, w_v; /* terminal cost w_soc max(0, soc_ref - soc) + w_v (v - v_ref)^2 */
+    int32_t n_lights;     /* traffic lights (Fig. 3) */
+    const int32_t *light_stage; /* [n_lights] distinct nodes in [1, n_stages - 1] */
+    const double *cycle, *red, *offset; /* [n_lights] s; red iff ((t - offset) mod cycle) < red */
+} dp_problem_desc;
+
+typedef struct dp_problem *dp_problem_t;
+
+/* Rollout output: caller-owned HOST arrays. */
+typedef struct dp_trajectory {
+    double *v, *soc, *t; /* [n_stages + 1] states along the route */
+    int32_t *u;          /* [n_stages] applied control index */
+    double *dt;          /* [n_stages] driving time of each step, s */
+    double *wait;        /* [n_stages] standstill at a red light before the step, s */
+    double *fuel;        /* [n_stages] fuel burnt in each step, g */
+    double fuel_g;       /* out: total fuel, g */
+    double time_s;       /* out: total time, s */
+    double J;            /* out: total cost including the terminal cost */
+    int32_t fail_stage;  /* out: first stage without a feasible control, or -1 */
+} dp_trajectory;
+
+/* Validate desc, allocate the problem's device state (value function for
+ * all N+1 stages, policy for N stages, per-stage scratch) and copy the
+ * problem tables to the device on `stream`.  Errors: DP_ERR_INVALID_ARG
+ * (sizes < limits above, non-finite parameters, lights not at distinct
+ * nodes in [1, N-1], n_te * n_tm * n_brake > 32767), DP_ERR_OOM,
+ * DP_ERR_CUDA. */
+dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *alloc, void *stream,
+                            dp_problem_t *out);
+
+/* Replace the problem's route data and parameters (grade, lights, model
+ * constants; Eq. 5-8) with those of desc, which must have the same sizes
+ * (stages, grids, controls) and light count; asynchronous on stream.
+ * Previously computed results become stale (DP_ERR_NOT_SOLVED). */
+dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *stream);
+
+/* Free everything (through the caller's allocator). NULL is accepted. */
+dp_status dp_problem_destroy(dp_problem_t p);
+
+/* Backward recursion of Eq. (9a)-(9d): J_N = c_T on the grid, then for
+ * k = N-1 .. 0 the per-state minimum over all controls of the stage cost
+ * plus the trilinearly interpolated J_{k+1} at the successor, with the
+ * argmin (lowest control index on exact ties).  Asynchronous on stream;
+ * results stay on the device.  The 2N+1 launches are captured in a CUDA graph
+ * on the first call on a stream and replayed afterwards. */
+dp_status dp_solve_backward(dp_problem_t p, void *stream);
+
+/* Copy J_stage (stage in [0, N]) or pi_stage (stage in [0, N-1]) into
+ * `out` (device memory, or host memory when out_is_host; the host copy
+ * synchronises the stream).  DP_ERR_NOT_SOLVED before a solve. */
+dp_status dp_get_value(dp_problem_t p, int32_t stage, float *out, int32_t out_is_host, void *stream);
+dp_status dp_get_policy(dp_problem_t p, int32_t stage, int16_t *out, int32_t out_is_host, void *stream);
+
+/* One stage of the recursion in isolation: J_k and pi_k from a given J_{k+1}
+ * (float32 [n_v][n_soc][n_t], +INFINITY = infeasible), device or host
+ * memory as flagged.  Outputs go to v_out / pi_out (either may be NULL)
+ * with the same location flag.  Used to compare single stages; it does not
+ * change the stored solution. */
+dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t v_next_is_host, float *v_out,
+                         int16_t *pi_out, int32_t out_is_host, void *stream);
+
+/* Forward rollout from x0 = {v, soc, t} (host array) through the stored
+ * J_1..J_N: at each stage every control is evaluated at the continuous
+ * state, the argmin (lowest index on ties) is applied, and fuel and time are
+ * summed in FP64 on the device.  Fills the caller's host trajectory and
+ * synchronises the stream.  DP_ERR_INFEASIBLE if a stage has no feasible
+ * control (traj->fail_stage tells which); DP_ERR_NOT_SOLVED before a solve. */
+dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream);
+
+/* Human-readable name of a status, and the last error message of the
+ * calling thread (empty string if none). */
+const char *dp_status_string(dp_status s);
+const char *dp_last_error(void);
+
+/* Sizes of the problem (for marshalling): fills n_stages, n_v, n_soc, n_t,
+ * n_controls. */
+dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5]);
+
+/* Select the Bellman kernel of later solves: 1 = tiled (default: torque
+ * classes, register windows, shared-memory tables), 0 = direct (one thread
+ * per state, every control read separately; the layout of the paper's
+ * second kernel, Sec. IV).  Both return bit-identical values and policies;
+ * the direct one exists for cross-checking.  DP_ERR_INVALID_ARG otherwise. */
+dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant);
+
+/* Profiling hook: run one backward sweep (same work and results as
+ * dp_solve_backward) with direct launches and CUDA events around every
+ * kernel, synchronise, and report milliseconds: ms[0] terminal values,
+ * ms[1] all N precompute launches, ms[2] all N Bellman launches, ms[3] the
+ * whole sweep. */
+dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4]);
+
+/* Counters of the last sweep (synchronises the stream): out[0] = state x
+ * control evaluations whose control passed the per-(speed, control) checks
+ * (effective evaluations, summed over stages), out[1] = state x torque-class
+ * pairs evaluated, out[2] = bytes one dp_problem_update copies host to
+ * device, out[3] = bytes one dp_rollout copies device to host.
+ * DP_ERR_NOT_SOLVED before a sweep. */
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[4], void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECODP_H */

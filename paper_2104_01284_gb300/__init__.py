@@ -1,0 +1,22 @@
+"""GB300-native dynamic-programming solver for look-ahead eco-driving.
+
+Implements the backward DP sweep and forward rollout of Zhu et al., "A GPU
+Implementation of a Look-Ahead Optimal Controller for Eco-Driving Based on
+Dynamic Programming" (ECC 2021) as hand-written sm_103a CUDA kernels behind
+a C ABI (include/ecodp.h, libecodp.so).
+
+Modules:
+  problems  seeded synthetic problem instances (no solver arithmetic)
+  native    ctypes binding of libecodp.so (fails loudly if it is not built)
+  solver    EcoDP: PyTorch-facing wrapper (device memory, streams)
+  build     nvcc build of libecodp.so
+"""
+
+__all__ = ["EcoDP", "problems"]
+
+
+def __getattr__(name):
+    if name == "EcoDP":
+        from .solver import EcoDP
+        return EcoDP
+    raise AttributeError(name)

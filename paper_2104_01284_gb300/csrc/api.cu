@@ -1,0 +1,665 @@
+// C ABI of the ecodp solver (declared in include/ecodp.h): problem objects,
+// validation, device memory through the caller's allocator, the CUDA-graph
+// captured backward sweep, result copies and the rollout.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ecodp.h"
+#include "ecodp_internal.cuh"
+
+using namespace ecodp;
+
+namespace ecodp {
+size_t bellman_smem_bytes(const DevParams &hP, bool smem_splits);
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dp_status fail(dp_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define DP_CUDA(call)                                                                             \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(DP_ERR_CUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
+    } while (0)
+
+}  // namespace
+
+struct dp_problem {
+    int N = 0, n_v = 0, n_xi = 0, n_t = 0, n_u = 0, n_lights = 0;
+    DevParams hP{};
+    dp_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t create_stream = nullptr;
+    std::vector<void *> blocks;
+
+    DevParams *dP = nullptr;
+    float *d_grade = nullptr;
+    int *d_lon = nullptr;
+    float *d_cyc = nullptr, *d_red = nullptr, *d_off = nullptr;
+    float *d_V = nullptr;
+    size_t stage_elems = 0;
+    int16_t *d_pi = nullptr;
+    size_t pi_elems = 0;
+    ClassRec *d_cls = nullptr;
+    ClassEntry *d_ent = nullptr;
+    int *d_rowcnt = nullptr;
+    float4 *d_spl = nullptr;
+    float *d_pad_in = nullptr, *d_pad_out = nullptr, *d_dense = nullptr;
+    int16_t *d_pi_tmp = nullptr;
+    double *d_roll = nullptr;
+    int *d_roll_u = nullptr;
+    unsigned long long *d_stats = nullptr;
+
+    // host copies of the tables (kept until the next update)
+    std::vector<float> h_grade, h_cyc, h_red, h_off;
+    std::vector<int> h_lon;
+
+    bool solved = false;
+    int variant = 1;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+
+    StageTables tables() const { return StageTables{d_grade, d_lon, d_cyc, d_red, d_off}; }
+    StageScratch scratch() const { return StageScratch{d_cls, d_ent, d_rowcnt, d_spl, d_stats}; }
+    float *V(int k) const { return d_V + (size_t)k * stage_elems; }
+    int16_t *pi(int k) const { return d_pi + (size_t)k * pi_elems; }
+};
+
+namespace {
+
+bool finite_all(std::initializer_list<double> xs)
+{
+    for (double x : xs)
+        if (!std::isfinite(x))
+            return false;
+    return true;
+}
+
+dp_status validate(const dp_problem_desc *d)
+{
+    if (!d)
+        return fail(DP_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n_stages < 1 || d->n_stages > 100000)
+        return fail(DP_ERR_INVALID_ARG, "n_stages must be in [1, 100000]");
+    if (d->n_v < 2 || d->n_soc < 2 || d->n_t < 2)
+        return fail(DP_ERR_INVALID_ARG, "state grids need at least 2 nodes");
+    if (d->n_v > 4096 || d->n_soc > 4096 || d->n_t > 4096)
+        return fail(DP_ERR_INVALID_ARG, "state grids are limited to 4096 nodes per axis");
+    if (d->n_te < 1 || d->n_tm < 1 || (d->n_brake != 1 && d->n_brake != 2))
+        return fail(DP_ERR_INVALID_ARG, "control grids need n_te, n_tm >= 1 and n_brake in {1, 2}");
+    if ((long long)d->n_te * d->n_tm * d->n_brake > 32767)
+        return fail(DP_ERR_INVALID_ARG, "at most 32767 controls (int16 policy)");
+    if (!d->grade)
+        return fail(DP_ERR_INVALID_ARG, "grade is NULL");
+    if (!finite_all({d->ds, d->v_lo, d->v_hi, d->soc_lo, d->soc_hi, d->t_lo, d->t_hi, d->te_lo, d->te_hi,
+                     d->tm_lo, d->tm_hi, d->brake_decel, d->a_min, d->a_max, d->mass, d->cda, d->crr, d->rho,
+                     d->g, d->r_wheel, d->gear, d->eta_motor, d->voc, d->r0, d->capacity_As, d->fuel_scale,
+                     d->gamma, d->soc_ref, d->w_soc, d->v_ref, d->w_v, d->fuel_coef[0], d->fuel_coef[1],
+                     d->fuel_coef[2], d->fuel_coef[3], d->fuel_coef[4], d->fuel_coef[5]}))
+        return fail(DP_ERR_INVALID_ARG, "non-finite parameter");
+    if (!(d->ds > 0 && d->v_hi > d->v_lo && d->v_lo >= 0 && d->soc_hi > d->soc_lo && d->t_hi > d->t_lo))
+        return fail(DP_ERR_INVALID_ARG, "need ds > 0, 0 <= v_lo < v_hi, soc_lo < soc_hi, t_lo < t_hi");
+    if (!(d->te_hi >= d->te_lo && d->tm_hi >= d->tm_lo && d->te_lo >= 0))
+        return fail(DP_ERR_INVALID_ARG, "torque grids need lo <= hi and te_lo >= 0");
+    if ((d->n_te == 1 && d->te_hi != d->te_lo) || (d->n_tm == 1 && d->tm_hi != d->tm_lo))
+        return fail(DP_ERR_INVALID_ARG, "a one-point torque grid needs lo == hi");
+    if (!(d->mass > 0 && d->r_wheel > 0 && d->gear > 0 && d->eta_motor > 0 && d->eta_motor <= 1 && d->voc > 0 &&
+          d->r0 > 0 && d->capacity_As > 0 && d->gamma >= 0 && d->gamma <= 1 && d->a_min <= d->a_max &&
+          d->w_soc >= 0 && d->w_v >= 0 && d->fuel_scale >= 0 && d->g >= 0 && d->cda >= 0 && d->crr >= 0))
+        return fail(DP_ERR_INVALID_ARG, "model parameter out of range");
+    double vmax = std::fmax(std::fabs(d->v_hi - d->v_ref), std::fabs(d->v_lo - d->v_ref));
+    if (d->w_soc * std::fabs(d->soc_ref - d->soc_lo) + d->w_v * vmax * vmax > 1e9)
+        return fail(DP_ERR_INVALID_ARG, "terminal cost weights too large (costs must stay below 1e9)");
+    for (int q = 0; q < d->n_stages; ++q)
+        if (!std::isfinite(d->grade[q]) || std::fabs(d->grade[q]) > 1.0)
+            return fail(DP_ERR_INVALID_ARG, "grade must be finite with |grade| <= 1");
+    if (d->n_lights < 0 || d->n_lights > d->n_stages)
+        return fail(DP_ERR_INVALID_ARG, "bad n_lights");
+    if (d->n_lights > 0 && (!d->light_stage || !d->cycle || !d->red || !d->offset))
+        return fail(DP_ERR_INVALID_ARG, "light arrays are NULL");
+    std::vector<char> seen(d->n_stages + 1, 0);
+    for (int q = 0; q < d->n_lights; ++q) {
+        int s = d->light_stage[q];
+        if (s < 1 || s > d->n_stages - 1 || seen[s])
+            return fail(DP_ERR_INVALID_ARG, "lights must sit at distinct nodes in [1, n_stages - 1]");
+        seen[s] = 1;
+        if (!finite_all({d->cycle[q], d->red[q], d->offset[q]}) || !(d->cycle[q] > 0) || d->red[q] < 0 ||
+            d->red[q] > d->cycle[q])
+            return fail(DP_ERR_INVALID_ARG, "light cycle/red/offset out of range");
+    }
+    return DP_OK;
+}
+
+float f32(double x) { return (float)x; }
+
+void fill_params(const dp_problem_desc *d, DevParams &P)
+{
+    P.N = d->n_stages;
+    P.n_v = d->n_v;
+    P.n_xi = d->n_soc;
+    P.n_t = d->n_t;
+    P.n_te = d->n_te;
+    P.n_tm = d->n_tm;
+    P.n_b = d->n_brake;
+    P.n_u = d->n_te * d->n_tm * d->n_brake;
+    // torque classes: when both torque grids share one step, controls with
+    // i_e + i_m equal have the same total torque
+    double he = d->n_te > 1 ? (d->te_hi - d->te_lo) / (d->n_te - 1) : 0.0;
+    double hm = d->n_tm > 1 ? (d->tm_hi - d->tm_lo) / (d->n_tm - 1) : 0.0;
+    bool same_step = (d->n_te == 1 || d->n_tm == 1) ? true : (he == hm);
+    P.class_sum = same_step ? 1 : 0;
+    P.n_cls = (same_step ? (d->n_te + d->n_tm - 1) : (d->n_te * d->n_tm)) * d->n_brake;
+    P.ld_t = round_up(d->n_t + 1, 4);
+    P.xi_rows = d->n_soc + 2;
+    P.n_lights = d->n_lights;
+    P.v_lo = f32(d->v_lo);
+    P.v_span = f32(d->v_hi - d->v_lo);
+    P.xi_lo = f32(d->soc_lo);
+    P.xi_span = f32(d->soc_hi - d->soc_lo);
+    P.t_lo = f32(d->t_lo);
+    P.t_span = f32(d->t_hi - d->t_lo);
+    P.te_lo = f32(d->te_lo);
+    P.te_span = f32(d->te_hi - d->te_lo);
+    P.tm_lo = f32(d->tm_lo);
+    P.tm_span = f32(d->tm_hi - d->tm_lo);
+    P.h_v = f32((d->v_hi - d->v_lo) / (d->n_v - 1));
+    P.h_xi = f32((d->soc_hi - d->soc_lo) / (d->n_soc - 1));
+    P.h_t = f32((d->t_hi - d->t_lo) / (d->n_t - 1));
+    P.ds = f32(d->ds);
+    P.mass = f32(d->mass);
+    P.g = f32(d->g);
+    P.crr = f32(d->crr);
+    P.half_rho_cda = f32(0.5 * d->rho * d->cda);
+    P.ratio = f32(d->gear / d->r_wheel);
+    P.brake_force = f32(d->mass * d->brake_decel);
+    P.a_min = f32(d->a_min);
+    P.a_max = f32(d->a_max);
+    P.eta = f32(d->eta_motor);
+    P.voc = f32(d->voc);
+    P.r0 = f32(d->r0);
+    P.cap = f32(d->capacity_As);
+    for (int q = 0; q < 6; ++q)
+        P.fc[q] = f32(d->fuel_coef[q]);
+    P.fuel_scale = f32(d->fuel_scale);
+    P.gamma = f32(d->gamma);
+    P.soc_ref = f32(d->soc_ref);
+    P.w_soc = f32(d->w_soc);
+    P.v_ref = f32(d->v_ref);
+    P.w_v = f32(d->w_v);
+}
+
+void fill_tables(const dp_problem_desc *d, dp_problem *p)
+{
+    p->h_grade.assign(d->n_stages, 0.f);
+    for (int q = 0; q < d->n_stages; ++q)
+        p->h_grade[q] = f32(d->grade[q]);
+    int nl = d->n_lights;
+    p->h_cyc.assign(nl > 0 ? nl : 1, 1.f);
+    p->h_red.assign(nl > 0 ? nl : 1, 0.f);
+    p->h_off.assign(nl > 0 ? nl : 1, 0.f);
+    p->h_lon.assign(d->n_stages + 1, -1);
+    for (int q = 0; q < nl; ++q) {
+        p->h_cyc[q] = f32(d->cycle[q]);
+        p->h_red[q] = f32(d->red[q]);
+        p->h_off[q] = f32(d->offset[q]);
+        p->h_lon[d->light_stage[q]] = q;
+    }
+}
+
+dp_status dev_alloc(dp_problem *p, size_t bytes, void **out)
+{
+    void *ptr = nullptr;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (p->has_alloc) {
+        ptr = p->alloc.alloc(bytes, (void *)p->create_stream, p->alloc.ctx);
+        if (!ptr)
+            return fail(DP_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    } else {
+        cudaError_t e = cudaMallocAsync(&ptr, bytes, p->create_stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA,
+                        std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        }
+    }
+    p->blocks.push_back(ptr);
+    *out = ptr;
+    return DP_OK;
+}
+
+template <class T>
+dp_status dev_alloc_n(dp_problem *p, size_t n, T **out)
+{
+    void *v = nullptr;
+    dp_status s = dev_alloc(p, n * sizeof(T), &v);
+    *out = (T *)v;
+    return s;
+}
+
+void release(dp_problem *p)
+{
+    if (p->gexec)
+        cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    if (p->cap_stream)
+        cudaStreamDestroy(p->cap_stream);
+    p->cap_stream = nullptr;
+    if (!p->blocks.empty())
+        cudaStreamSynchronize(p->create_stream);
+    for (void *b : p->blocks) {
+        if (p->has_alloc)
+            p->alloc.free(b, (void *)p->create_stream, p->alloc.ctx);
+        else
+            cudaFree(b);
+    }
+    p->blocks.clear();
+}
+
+dp_status upload_tables(dp_problem *p, cudaStream_t s)
+{
+    DP_CUDA(cudaMemcpyAsync(p->dP, &p->hP, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_grade, p->h_grade.data(), p->h_grade.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_lon, p->h_lon.data(), p->h_lon.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_cyc, p->h_cyc.data(), p->h_cyc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_red, p->h_red.data(), p->h_red.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_off, p->h_off.data(), p->h_off.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    return DP_OK;
+}
+
+// The backward sweep's launches (terminal values, then per stage the
+// precompute and Bellman kernels).
+dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
+{
+    DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 2 * sizeof(unsigned long long), s));
+    DP_CUDA(launch_terminal(p->dP, p->hP, p->V(p->N), s));
+    for (int k = p->N - 1; k >= 0; --k) {
+        DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, p->scratch(), s));
+        DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->V(k + 1), p->V(k), p->pi(k),
+                               p->variant, s));
+    }
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dp_status_string(dp_status s)
+{
+    switch (s) {
+    case DP_OK: return "DP_OK";
+    case DP_ERR_INVALID_ARG: return "DP_ERR_INVALID_ARG";
+    case DP_ERR_OOM: return "DP_ERR_OOM";
+    case DP_ERR_CUDA: return "DP_ERR_CUDA";
+    case DP_ERR_INFEASIBLE: return "DP_ERR_INFEASIBLE";
+    case DP_ERR_NOT_SOLVED: return "DP_ERR_NOT_SOLVED";
+    case DP_ERR_TIMEOUT: return "DP_ERR_TIMEOUT";
+    case DP_ERR_INTERNAL: return "DP_ERR_INTERNAL";
+    }
+    return "DP_ERR_UNKNOWN";
+}
+
+const char *dp_last_error(void) { return g_last_error.c_str(); }
+
+dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *alloc, void *stream, dp_problem_t *out)
+{
+    if (!out)
+        return fail(DP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    dp_status st = validate(desc);
+    if (st != DP_OK)
+        return st;
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(DP_ERR_INVALID_ARG, "allocator needs both alloc and free");
+    dp_problem *p = new (std::nothrow) dp_problem();
+    if (!p)
+        return fail(DP_ERR_OOM, "host allocation failed");
+    p->create_stream = (cudaStream_t)stream;
+    if (alloc) {
+        p->alloc = *alloc;
+        p->has_alloc = true;
+    }
+    fill_params(desc, p->hP);
+    fill_tables(desc, p);
+    p->N = desc->n_stages;
+    p->n_v = desc->n_v;
+    p->n_xi = desc->n_soc;
+    p->n_t = desc->n_t;
+    p->n_u = p->hP.n_u;
+    p->n_lights = desc->n_lights;
+    const DevParams &P = p->hP;
+    p->stage_elems = (size_t)P.n_v * P.xi_rows * P.ld_t;
+    p->pi_elems = (size_t)P.n_v * P.n_xi * P.n_t;
+    if (const char *e = std::getenv("ECODP_GRAPH"))
+        p->use_graph = std::atoi(e) != 0;
+
+#define TRY(x)              \
+    do {                    \
+        st = (x);           \
+        if (st != DP_OK) {  \
+            release(p);     \
+            delete p;       \
+            return st;      \
+        }                   \
+    } while (0)
+    TRY(dev_alloc_n(p, 1, &p->dP));
+    TRY(dev_alloc_n(p, p->h_grade.size(), &p->d_grade));
+    TRY(dev_alloc_n(p, p->h_lon.size(), &p->d_lon));
+    TRY(dev_alloc_n(p, p->h_cyc.size(), &p->d_cyc));
+    TRY(dev_alloc_n(p, p->h_red.size(), &p->d_red));
+    TRY(dev_alloc_n(p, p->h_off.size(), &p->d_off));
+    TRY(dev_alloc_n(p, p->stage_elems * (size_t)(p->N + 1), &p->d_V));
+    TRY(dev_alloc_n(p, p->pi_elems * (size_t)p->N, &p->d_pi));
+    TRY(dev_alloc_n(p, (size_t)P.n_v * P.n_cls, &p->d_cls));
+    TRY(dev_alloc_n(p, (size_t)P.n_v * P.n_cls, &p->d_ent));
+    TRY(dev_alloc_n(p, (size_t)P.n_v * 2, &p->d_rowcnt));
+    TRY(dev_alloc_n(p, (size_t)P.n_v * P.n_u, &p->d_spl));
+    TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_in));
+    TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_out));
+    TRY(dev_alloc_n(p, p->pi_elems, &p->d_dense));
+    TRY(dev_alloc_n(p, p->pi_elems, &p->d_pi_tmp));
+    TRY(dev_alloc_n(p, (size_t)(3 * (P.N + 1) + 3 * P.N + 4), &p->d_roll));
+    TRY(dev_alloc_n(p, (size_t)P.N, &p->d_roll_u));
+    TRY(dev_alloc_n(p, (size_t)2, &p->d_stats));
+    TRY(upload_tables(p, p->create_stream));
+    auto cuda_try = [&](cudaError_t e, const char *what) -> dp_status {
+        if (e != cudaSuccess)
+            return fail(DP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        return DP_OK;
+    };
+    // every padding cell holds the infeasible sentinel for the object's life
+    TRY(cuda_try(launch_fill(p->d_V, p->stage_elems * (size_t)(p->N + 1), V_BIG, p->create_stream), "fill V"));
+    TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
+    TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
+    TRY(cuda_try(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
+    size_t smem = bellman_smem_bytes(P, bellman_smem_bytes(P, true) <= 160 * 1024);
+    if (smem > 227 * 1024) {
+        release(p);
+        delete p;
+        return fail(DP_ERR_INVALID_ARG, "too many torque classes for the shared-memory tables");
+    }
+#undef TRY
+    *out = p;
+    return DP_OK;
+}
+
+dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *stream)
+{
+    if (!p)
+        return fail(DP_ERR_INVALID_ARG, "problem is NULL");
+    dp_status st = validate(desc);
+    if (st != DP_OK)
+        return st;
+    if (desc->n_stages != p->N || desc->n_v != p->n_v || desc->n_soc != p->n_xi || desc->n_t != p->n_t ||
+        desc->n_te * desc->n_tm * desc->n_brake != p->n_u || desc->n_te != p->hP.n_te ||
+        desc->n_brake != p->hP.n_b || desc->n_lights != p->n_lights)
+        return fail(DP_ERR_INVALID_ARG, "update must keep the problem's sizes and light count");
+    DevParams P;
+    fill_params(desc, P);
+    if (P.n_cls != p->hP.n_cls)
+        return fail(DP_ERR_INVALID_ARG, "update changes the torque class structure");
+    p->hP = P;
+    fill_tables(desc, p);
+    st = upload_tables(p, (cudaStream_t)stream);
+    p->solved = false;
+    return st;
+}
+
+dp_status dp_problem_destroy(dp_problem_t p)
+{
+    if (!p)
+        return DP_OK;
+    release(p);
+    delete p;
+    return DP_OK;
+}
+
+dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5])
+{
+    if (!p || !sizes)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    sizes[0] = p->N;
+    sizes[1] = p->n_v;
+    sizes[2] = p->n_xi;
+    sizes[3] = p->n_t;
+    sizes[4] = p->n_u;
+    return DP_OK;
+}
+
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[4], void *stream)
+{
+    if (!p || !out)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    if (!p->solved)
+        return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
+    unsigned long long h[2] = {0, 0};
+    cudaStream_t s = (cudaStream_t)stream;
+    DP_CUDA(cudaMemcpyAsync(h, p->d_stats, sizeof h, cudaMemcpyDeviceToHost, s));
+    DP_CUDA(cudaStreamSynchronize(s));
+    out[0] = (int64_t)h[0] * p->n_xi * p->n_t;
+    out[1] = (int64_t)h[1] * p->n_xi * p->n_t;
+    // bytes of one dp_problem_update (tables) and one dp_rollout (trajectory)
+    out[2] = (int64_t)(sizeof(DevParams) + p->h_grade.size() * sizeof(float) + p->h_lon.size() * sizeof(int) +
+                       3 * p->h_cyc.size() * sizeof(float));
+    out[3] = (int64_t)((3 * (p->N + 1) + 3 * p->N + 4) * sizeof(double) + p->N * sizeof(int));
+    return DP_OK;
+}
+
+dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant)
+{
+    if (!p || (variant != 0 && variant != 1))
+        return fail(DP_ERR_INVALID_ARG, "variant must be 0 (direct) or 1 (tiled)");
+    if (variant != p->variant) {
+        p->variant = variant;
+        if (p->gexec)
+            cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return DP_OK;
+}
+
+dp_status dp_solve_backward(dp_problem_t p, void *stream)
+{
+    if (!p)
+        return fail(DP_ERR_INVALID_ARG, "problem is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->use_graph) {
+        dp_status st = enqueue_sweep(p, s);
+        if (st != DP_OK)
+            return st;
+        p->solved = true;
+        return DP_OK;
+    }
+    if (!p->gexec) {
+        cudaGraph_t g = nullptr;
+        DP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        dp_status st = enqueue_sweep(p, p->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (st != DP_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess)
+            return fail(DP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            return fail(DP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    DP_CUDA(cudaGraphLaunch(p->gexec, s));
+    p->solved = true;
+    return DP_OK;
+}
+
+dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
+{
+    if (!p || !ms)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = p->N;
+    std::vector<cudaEvent_t> ev(2 * N + 2, nullptr);
+    for (auto &e : ev)
+        DP_CUDA(cudaEventCreate(&e));
+    dp_status st = DP_OK;
+    auto run = [&]() -> dp_status {
+        DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 2 * sizeof(unsigned long long), s));
+        DP_CUDA(cudaEventRecord(ev[0], s));
+        DP_CUDA(launch_terminal(p->dP, p->hP, p->V(N), s));
+        DP_CUDA(cudaEventRecord(ev[1], s));
+        for (int k = N - 1, q = 1; k >= 0; --k, q += 2) {
+            DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, p->scratch(), s));
+            DP_CUDA(cudaEventRecord(ev[q + 1], s));
+            DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->V(k + 1), p->V(k), p->pi(k),
+                                   p->variant, s));
+            DP_CUDA(cudaEventRecord(ev[q + 2], s));
+        }
+        DP_CUDA(cudaEventSynchronize(ev[2 * N + 1]));
+        float t = 0.f, pre = 0.f, bell = 0.f, all = 0.f;
+        DP_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+        for (int q = 1; q < 2 * N + 1; q += 2) {
+            float a = 0.f, b = 0.f;
+            DP_CUDA(cudaEventElapsedTime(&a, ev[q], ev[q + 1]));
+            DP_CUDA(cudaEventElapsedTime(&b, ev[q + 1], ev[q + 2]));
+            pre += a;
+            bell += b;
+        }
+        DP_CUDA(cudaEventElapsedTime(&all, ev[0], ev[2 * N + 1]));
+        ms[0] = t;
+        ms[1] = pre;
+        ms[2] = bell;
+        ms[3] = all;
+        return DP_OK;
+    };
+    st = run();
+    for (auto &e : ev)
+        cudaEventDestroy(e);
+    if (st == DP_OK)
+        p->solved = true;
+    return st;
+}
+
+dp_status dp_get_value(dp_problem_t p, int32_t stage, float *out, int32_t out_is_host, void *stream)
+{
+    if (!p || !out)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    if (stage < 0 || stage > p->N)
+        return fail(DP_ERR_INVALID_ARG, "stage out of range");
+    if (!p->solved)
+        return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
+    cudaStream_t s = (cudaStream_t)stream;
+    float *dst = out_is_host ? p->d_dense : out;
+    DP_CUDA(launch_dense_from_pad(p->hP, p->V(stage), dst, s));
+    if (out_is_host) {
+        DP_CUDA(cudaMemcpyAsync(out, p->d_dense, p->pi_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
+        DP_CUDA(cudaStreamSynchronize(s));
+    }
+    return DP_OK;
+}
+
+dp_status dp_get_policy(dp_problem_t p, int32_t stage, int16_t *out, int32_t out_is_host, void *stream)
+{
+    if (!p || !out)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    if (stage < 0 || stage >= p->N)
+        return fail(DP_ERR_INVALID_ARG, "stage out of range");
+    if (!p->solved)
+        return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
+    cudaStream_t s = (cudaStream_t)stream;
+    DP_CUDA(cudaMemcpyAsync(out, p->pi(stage), p->pi_elems * sizeof(int16_t),
+                            out_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (out_is_host)
+        DP_CUDA(cudaStreamSynchronize(s));
+    return DP_OK;
+}
+
+dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t v_next_is_host, float *v_out,
+                         int16_t *pi_out, int32_t out_is_host, void *stream)
+{
+    if (!p || !v_next)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    if (k < 0 || k >= p->N)
+        return fail(DP_ERR_INVALID_ARG, "stage out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = p->pi_elems;
+    DP_CUDA(cudaMemcpyAsync(p->d_dense, v_next, n * sizeof(float),
+                            v_next_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    StageScratch sc = p->scratch();
+    sc.stats = nullptr;
+    DP_CUDA(launch_pad_from_dense(p->hP, p->d_dense, p->d_pad_in, s));
+    DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, sc, s));
+    DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, sc, p->d_pad_in, p->d_pad_out, p->d_pi_tmp, p->variant, s));
+    if (v_out) {
+        DP_CUDA(launch_dense_from_pad(p->hP, p->d_pad_out, p->d_dense, s));
+        DP_CUDA(cudaMemcpyAsync(v_out, p->d_dense, n * sizeof(float),
+                                out_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    }
+    if (pi_out)
+        DP_CUDA(cudaMemcpyAsync(pi_out, p->d_pi_tmp, n * sizeof(int16_t),
+                                out_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (out_is_host)
+        DP_CUDA(cudaStreamSynchronize(s));
+    return DP_OK;
+}
+
+dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream)
+{
+    if (!p || !x0 || !traj)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    if (!traj->v || !traj->soc || !traj->t || !traj->u || !traj->dt || !traj->wait || !traj->fuel)
+        return fail(DP_ERR_INVALID_ARG, "trajectory arrays must all be provided");
+    if (!finite_all({x0[0], x0[1], x0[2]}))
+        return fail(DP_ERR_INVALID_ARG, "x0 must be finite");
+    if (!p->solved)
+        return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = p->N;
+    DP_CUDA(launch_rollout(p->dP, p->hP, p->tables(), p->d_V, p->stage_elems, x0[0], x0[1], x0[2], p->d_roll,
+                           p->d_roll_u, s));
+    std::vector<double> h(3 * (N + 1) + 3 * N + 4);
+    std::vector<int> hu(N, -1);
+    DP_CUDA(cudaMemcpyAsync(h.data(), p->d_roll, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DP_CUDA(cudaMemcpyAsync(hu.data(), p->d_roll_u, hu.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DP_CUDA(cudaStreamSynchronize(s));
+    const double *tot = h.data() + 3 * (N + 1) + 3 * N;
+    int fail_stage = (int)tot[3];
+    int reached = fail_stage >= 0 ? fail_stage : N;
+    for (int q = 0; q <= N; ++q) {
+        bool ok = q <= reached;
+        traj->v[q] = ok ? h[3 * q] : NAN;
+        traj->soc[q] = ok ? h[3 * q + 1] : NAN;
+        traj->t[q] = ok ? h[3 * q + 2] : NAN;
+    }
+    for (int q = 0; q < N; ++q) {
+        bool ok = q < reached;
+        traj->u[q] = ok ? hu[q] : -1;
+        traj->dt[q] = ok ? h[3 * (N + 1) + q] : NAN;
+        traj->wait[q] = ok ? h[3 * (N + 1) + N + q] : NAN;
+        traj->fuel[q] = ok ? h[3 * (N + 1) + 2 * N + q] : NAN;
+    }
+    traj->fuel_g = tot[0];
+    traj->time_s = tot[1];
+    traj->J = tot[2];
+    traj->fail_stage = fail_stage;
+    if (fail_stage >= 0)
+        return fail(DP_ERR_INFEASIBLE, "no feasible control at stage " + std::to_string(fail_stage));
+    return DP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+// Internal types and FP32 device arithmetic shared by the ecodp kernels.
+//
+// Paper: Zhu et al., "A GPU Implementation of a Look-Ahead Optimal
+// Controller for Eco-Driving Based on Dynamic Programming", ECC 2021.
+//
+// Data layout in HBM (per problem):
+//   V   float [N+1][n_v][n_soc+2][ld_t]   value function of every stage.  Soc
+//       rows 0 and n_soc+1 and time columns >= n_t are padding that always
+//       holds V_BIG, so an interpolation corner that falls outside the grid
+//       reads an "infeasible" value without a branch.  ld_t = round_up(n_t+1,
+//       4) keeps every row 16-byte aligned.
+//   pi  int16 [N][n_v][n_soc][n_t]        argmin control index, -1 infeasible.
+//   per-stage scratch (rewritten at every stage by the precompute kernel):
+//       ClassRec  [n_v][n_cls]  speed/time transition of every torque class
+//       ClassEntry[n_v][n_cls]  the feasible classes of each speed row
+//       float4    [n_v][n_u]    per-control record {cost, w0, w1, u|d}
+//
+// Infeasibility is carried as the finite sentinel V_BIG instead of +inf: an
+// interpolation weight of exactly 0 (a snapped fraction) then contributes
+// exactly 0, and any non-zero weight (>= 1e-5 per axis, so >= 1e-15 for a
+// trilinear corner) lifts the sum above V_FEAS_MAX.  Results >= V_FEAS_MAX are
+// stored as V_BIG and reported to callers as +inf.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ecodp {
+
+constexpr float V_BIG = 1e30f;
+constexpr float V_FEAS_MAX = 1e12f;
+constexpr float SNAP = 1e-5f;
+
+// Bellman kernel tiling: each thread owns RJ consecutive SoC rows at one time
+// node; controls are grouped into torque classes (see ClassRec).
+constexpr int RJ = 8;
+
+struct DevParams {
+    // sizes
+    int N, n_v, n_xi, n_t, n_te, n_tm, n_b, n_u;
+    int n_cls;      // torque classes (see ClassRec)
+    int class_sum;  // 1: classes are the sums i_e + i_m (equal torque steps)
+    int ld_t, xi_rows;
+    int n_lights;
+    // grids: node i = lo + (span * i) / (n - 1)
+    float v_lo, v_span, xi_lo, xi_span, t_lo, t_span, te_lo, te_span, tm_lo, tm_span;
+    float h_v, h_xi, h_t;
+    float ds;
+    // model
+    float mass, g, crr, half_rho_cda, ratio, brake_force, a_min, a_max, eta, voc, r0, cap;
+    float fc[6];
+    float fuel_scale, gamma;
+    float soc_ref, w_soc, v_ref, w_v;
+};
+
+// A torque class: all controls with the same total torque T_eng + T_bsg and
+// brake flag share the speed update (Eq. 5a) and the step time (Eq. 2), hence
+// the speed-axis and time-axis interpolation of J_{k+1}.
+struct ClassRec {
+    int ok;     // feasible at class level (Eq. 7a, 7d, stopping rule)
+    int iv;     // lower speed node of v'
+    float fv;   // snapped weight of node iv + 1
+    float v1;   // v'
+    float dt;   // driving time of the step
+    int st;     // floor(dt / h_t) after snapping
+    float ft;   // snapped fraction of dt / h_t
+    int pad;
+};
+
+struct ClassEntry {
+    int cls;    // class index
+    int off;    // first split record of this class in the row's split array
+    int nb[4];  // splits with soc shift d = -2, -1, 0, +1
+    int n_other;  // splits with any other shift (after the four buckets)
+    int n_total;
+};
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+__device__ __forceinline__ float node_val(float lo, float span, int i, int n)
+{
+    return n > 1 ? __fadd_rn(lo, __fdiv_rn(__fmul_rn(span, (float)i), (float)(n - 1))) : lo;
+}
+
+// Position inside a light cycle in [0, cycle): red iff < red duration.
+__device__ __forceinline__ float phase_pos(float t, float offset, float cycle)
+{
+    float x = __fsub_rn(t, offset);
+    float ph = __fsub_rn(x, __fmul_rn(cycle, floorf(__fdiv_rn(x, cycle))));
+    if (ph < 0.f)
+        ph = __fadd_rn(ph, cycle);
+    if (ph >= cycle)
+        ph = __fsub_rn(ph, cycle);
+    return ph;
+}
+
+// Snap a fraction: below SNAP -> 0, above 1 - SNAP -> next node.
+__device__ __forceinline__ void snap_split(float q, int &i, float &f)
+{
+    float fl = floorf(q);
+    i = (int)fl;
+    f = __fsub_rn(q, fl);
+    if (f < SNAP) {
+        f = 0.f;
+    } else if (f > 1.f - SNAP) {
+        f = 0.f;
+        i += 1;
+    }
+}
+
+// Engine torque and BSG torque of control u = (ie * n_tm + im) * n_b + b.
+__device__ __forceinline__ void decode_u(const DevParams &P, int u, int &ie, int &im, int &b)
+{
+    b = u % P.n_b;
+    int r = u / P.n_b;
+    im = r % P.n_tm;
+    ie = r / P.n_tm;
+}
+
+// ---- model pieces (FP32) ----------------------------------------------------
+
+// Road load at speed v on a slope with sin/cos theta (Eq. 5a).
+__device__ __forceinline__ float road_load(const DevParams &P, float v, float sin_th, float cos_th)
+{
+    float roll_grade = __fmul_rn(__fmul_rn(P.mass, P.g), __fadd_rn(__fmul_rn(P.crr, cos_th), sin_th));
+    return __fadd_rn(roll_grade, __fmul_rn(P.half_rho_cda, __fmul_rn(v, v)));
+}
+
+// Speed update and step time (Eq. 5a, Eq. 2) for total torque T and brake b
+// from speed v.  Returns false if infeasible.  next_light: the arrival node
+// holds a light (the vehicle may then stop at the line).
+__device__ __forceinline__ bool speed_step(const DevParams &P, float v, float F_road, float T, int b, bool next_light,
+                                           float &v1, float &dt)
+{
+    float F_tr = __fsub_rn(__fmul_rn(T, P.ratio), b ? P.brake_force : 0.f);
+    float a = __fdiv_rn(__fsub_rn(F_tr, F_road), P.mass);
+    if (a < P.a_min || a > P.a_max)
+        return false;
+    float R = __fadd_rn(__fmul_rn(v, v), __fmul_rn(__fmul_rn(2.f, P.ds), a));
+    if (R < 0.f) {
+        if (!(next_light && v > 0.f))
+            return false;
+        v1 = 0.f;
+        dt = __fdiv_rn(__fmul_rn(2.f, P.ds), v);
+        return true;
+    }
+    v1 = __fsqrt_rn(R);
+    float vs = __fadd_rn(v, v1);
+    if (!(vs > 0.f))
+        return false;
+    dt = __fdiv_rn(__fmul_rn(2.f, P.ds), vs);
+    return true;
+}
+
+// Fuel rate (g/s) of the engine at speed w (rad/s) and torque Te (Nm).
+__device__ __forceinline__ float fuel_rate(const DevParams &P, float w, float Te)
+{
+    if (!(Te > 0.f))
+        return 0.f;
+    float s = P.fc[0];
+    s = __fadd_rn(s, __fmul_rn(P.fc[1], w));
+    s = __fadd_rn(s, __fmul_rn(P.fc[2], Te));
+    s = __fadd_rn(s, __fmul_rn(__fmul_rn(P.fc[3], w), Te));
+    s = __fadd_rn(s, __fmul_rn(__fmul_rn(P.fc[4], w), w));
+    s = __fadd_rn(s, __fmul_rn(__fmul_rn(P.fc[5], Te), Te));
+    return __fmul_rn(P.fuel_scale, s);
+}
+
+// Battery current (A) for BSG torque Tm at crank speed w (Eq. 5b): zeroth-
+// order circuit, written as 2P / (Voc + sqrt(Voc^2 - 4 R0 P)), the cancellation
+// free form of the smaller root.  Returns false if the power exceeds what the
+// circuit can deliver.
+__device__ __forceinline__ bool battery_current(const DevParams &P, float w, float Tm, float &I)
+{
+    float Pm = __fmul_rn(Tm, w);
+    float Pb = Pm > 0.f ? __fdiv_rn(Pm, P.eta) : __fmul_rn(Pm, P.eta);
+    float disc = __fsub_rn(__fmul_rn(P.voc, P.voc), __fmul_rn(__fmul_rn(4.f, P.r0), Pb));
+    if (disc < 0.f)
+        return false;
+    I = __fdiv_rn(__fmul_rn(2.f, Pb), __fadd_rn(P.voc, __fsqrt_rn(disc)));
+    return true;
+}
+
+__device__ __forceinline__ float terminal_cost(const DevParams &P, float v, float xi)
+{
+    float sh = fmaxf(__fsub_rn(P.soc_ref, xi), 0.f);
+    float dv = __fsub_rn(v, P.v_ref);
+    return __fadd_rn(__fmul_rn(P.w_soc, sh), __fmul_rn(P.w_v, __fmul_rn(dv, dv)));
+}
+
+// Bilinear blend of two speed rows at two time columns.
+__device__ __forceinline__ float g_blend(const float *__restrict__ r0, const float *__restrict__ r1, int ta, int tb,
+                                         float wv0, float wv1, float wt0, float wt1)
+{
+    float A = __fmaf_rn(wv1, __ldg(r1 + ta), __fmul_rn(wv0, __ldg(r0 + ta)));
+    float B = __fmaf_rn(wv1, __ldg(r1 + tb), __fmul_rn(wv0, __ldg(r0 + tb)));
+    return __fmaf_rn(wt1, B, __fmul_rn(wt0, A));
+}
+
+// ---- launchers (host) -------------------------------------------------------
+
+struct StageTables {
+    const float *grade;        // [N]
+    const int *light_of_node;  // [N+1], -1 = none
+    const float *cycle, *red, *offset;
+};
+
+struct StageScratch {
+    ClassRec *cls;    // [n_v][n_cls]
+    ClassEntry *ent;  // [n_v][n_cls]
+    int *row_cnt;     // [n_v][2] feasible classes, splits
+    float4 *spl;      // [n_v][n_u]
+    unsigned long long *stats;  // [2] running totals: feasible (v, u) pairs, feasible (v, class) pairs
+};
+
+cudaError_t launch_fill(float *p, size_t n, float val, cudaStream_t s);
+cudaError_t launch_terminal(const DevParams *dP, const DevParams &hP, float *VN, cudaStream_t s);
+cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
+                              cudaStream_t s);
+cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
+                           const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s);
+cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float *padded, cudaStream_t s);
+cudaError_t launch_dense_from_pad(const DevParams &hP, const float *padded, float *dense, cudaStream_t s);
+cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
+                           size_t stage_elems, double v0, double xi0, double t0, double *out, int *out_u,
+                           cudaStream_t s);
+
+}  // namespace ecodp

@@ -1,0 +1,276 @@
+// Per-stage precompute (the paper's first kernel, Sec. IV), terminal values
+// and layout conversions.
+//
+// The paper's first kernel evaluates, per (v, T_eng, T_bsg), the speed change,
+// the step time, the battery power and the stage cost.  Here one CTA handles
+// one speed row v_i of stage k and writes
+//   * one ClassRec per torque class (speed update Eq. 5a, step time Eq. 2,
+//     acceleration limits Eq. 7d, stop-at-line rule, speed-grid band Eq. 7a)
+//     with the speed-axis and time-axis interpolation already resolved;
+//   * the compact list of feasible classes (ClassEntry) in class order;
+//   * per feasible control one float4 {cost, w0, w1, u | d << 16}: the stage
+//     cost of Eq. (1)/(6), and the SoC-axis shift d and weights (1-f, f) of
+//     xi' = xi - dt I / C_nom (Eq. 5b), grouped inside each class by d.
+#include "ecodp_internal.cuh"
+
+namespace ecodp {
+
+namespace {
+
+__global__ void fill_kernel(float *p, size_t n, float val)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = val;
+}
+
+__global__ void terminal_kernel(const DevParams *__restrict__ dP, float *__restrict__ VN)
+{
+    const DevParams &P = *dP;
+    int total = P.n_v * P.n_xi * P.n_t;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+        int l = s % P.n_t;
+        int j = (s / P.n_t) % P.n_xi;
+        int i = s / (P.n_t * P.n_xi);
+        float v = node_val(P.v_lo, P.v_span, i, P.n_v);
+        float xi = node_val(P.xi_lo, P.xi_span, j, P.n_xi);
+        VN[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] = terminal_cost(P, v, xi);
+    }
+}
+
+__global__ void pad_from_dense_kernel(const DevParams P, const float *__restrict__ dense, float *__restrict__ padded)
+{
+    int total = P.n_v * P.n_xi * P.n_t;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+        int l = s % P.n_t;
+        int j = (s / P.n_t) % P.n_xi;
+        int i = s / (P.n_t * P.n_xi);
+        float x = dense[s];
+        padded[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] = (x < V_FEAS_MAX) ? x : V_BIG;
+    }
+}
+
+__global__ void dense_from_pad_kernel(const DevParams P, const float *__restrict__ padded, float *__restrict__ dense)
+{
+    int total = P.n_v * P.n_xi * P.n_t;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+        int l = s % P.n_t;
+        int j = (s / P.n_t) % P.n_xi;
+        int i = s / (P.n_t * P.n_xi);
+        float x = padded[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l];
+        dense[s] = (x < V_FEAS_MAX) ? x : __int_as_float(0x7f800000);
+    }
+}
+
+// Members (i_e, i_m) of class c in increasing i_e order.
+struct Members {
+    int ie_lo, ie_hi, s;  // class_sum: i_m = s - i_e; otherwise one member
+    int im_single;
+};
+
+__device__ __forceinline__ Members class_members(const DevParams &P, int c)
+{
+    Members m;
+    int s = c / P.n_b;
+    if (P.class_sum) {
+        m.ie_lo = max(0, s - (P.n_tm - 1));
+        m.ie_hi = min(s, P.n_te - 1);
+        m.s = s;
+        m.im_single = -1;
+    } else {
+        m.ie_lo = m.ie_hi = s / P.n_tm;
+        m.im_single = s % P.n_tm;
+        m.s = -1;
+    }
+    return m;
+}
+
+__device__ __forceinline__ int member_im(const Members &m, int ie) { return m.im_single >= 0 ? m.im_single : m.s - ie; }
+
+// Block-wide exclusive scan of one int per thread; returns the prefix and
+// writes the block total.  buf holds blockDim.x + 1 ints.
+__device__ int block_exclusive_scan(int x, int *buf, int &total)
+{
+    int tid = threadIdx.x;
+    buf[tid] = x;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+        int y = tid >= off ? buf[tid - off] : 0;
+        __syncthreads();
+        buf[tid] += y;
+        __syncthreads();
+    }
+    int incl = buf[tid];
+    total = buf[blockDim.x - 1];
+    __syncthreads();
+    return incl - x;
+}
+
+__global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb, int k,
+                                                         StageScratch sc)
+{
+    __shared__ DevParams P;
+    __shared__ int scan_buf[256 + 1];
+    if (threadIdx.x == 0)
+        P = *dP;
+    __syncthreads();
+
+    const int i = blockIdx.x;
+    const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
+    const float p = tb.grade[k];
+    const float sq = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(p, p)));
+    const float sin_th = __fdiv_rn(p, sq), cos_th = __fdiv_rn(1.f, sq);
+    const float F_road = road_load(P, v, sin_th, cos_th);
+    const bool next_light = tb.light_of_node[k + 1] >= 0;
+    const float w = __fmul_rn(v, P.ratio);
+    const float one_m_gamma = __fsub_rn(1.f, P.gamma);
+
+    ClassRec *cls_row = sc.cls + (size_t)i * P.n_cls;
+    ClassEntry *ent_row = sc.ent + (size_t)i * P.n_cls;
+    float4 *spl_row = sc.spl + (size_t)i * P.n_u;
+
+    int ent_carry = 0, spl_carry = 0;
+    for (int c0 = 0; c0 < P.n_cls; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        ClassRec rec = {};
+        int nspl = 0;
+        Members mem = {};
+        if (c < P.n_cls) {
+            const int b = c % P.n_b;
+            mem = class_members(P, c);
+            const int ie0 = mem.ie_lo, im0 = member_im(mem, ie0);
+            const float T = __fadd_rn(node_val(P.te_lo, P.te_span, ie0, P.n_te),
+                                      node_val(P.tm_lo, P.tm_span, im0, P.n_tm));
+            float v1 = 0.f, dt = 0.f;
+            bool ok = speed_step(P, v, F_road, T, b, next_light, v1, dt);
+            if (ok) {
+                // speed-axis band (Eq. 7a) and interpolation cell
+                float qv = __fdiv_rn(__fsub_rn(v1, P.v_lo), P.h_v);
+                float top = (float)(P.n_v - 1);
+                if (qv < -SNAP || qv > top + SNAP)
+                    ok = false;
+                qv = fminf(fmaxf(qv, 0.f), top);
+                int iv;
+                float fv;
+                snap_split(qv, iv, fv);
+                if (iv >= P.n_v - 1) {
+                    iv = P.n_v - 2;
+                    fv = 1.f;
+                }
+                int st;
+                float ft;
+                snap_split(__fdiv_rn(dt, P.h_t), st, ft);
+                rec.iv = iv;
+                rec.fv = fv;
+                rec.v1 = v1;
+                rec.dt = dt;
+                rec.st = st;
+                rec.ft = ft;
+            }
+            rec.ok = ok;
+            if (ok) {
+                for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
+                    float I;
+                    float Tm = node_val(P.tm_lo, P.tm_span, member_im(mem, ie), P.n_tm);
+                    nspl += battery_current(P, w, Tm, I) ? 1 : 0;
+                }
+            }
+            cls_row[c] = rec;
+        }
+        const int feas = (c < P.n_cls && rec.ok && nspl > 0) ? 1 : 0;
+        int ent_tot, spl_tot;
+        const int ent_idx = block_exclusive_scan(feas, scan_buf, ent_tot) + ent_carry;
+        const int spl_off = block_exclusive_scan(feas ? nspl : 0, scan_buf, spl_tot) + spl_carry;
+        if (feas) {
+            const int b = c % P.n_b;
+            ClassEntry E;
+            E.cls = c;
+            E.off = spl_off;
+            E.n_total = nspl;
+            int pos = spl_off;
+            // buckets d = -2, -1, 0, +1, then every other shift
+            for (int bucket = 0; bucket < 5; ++bucket) {
+                int cnt = 0;
+                for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
+                    const int im = member_im(mem, ie);
+                    const float Te = node_val(P.te_lo, P.te_span, ie, P.n_te);
+                    const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
+                    float I;
+                    if (!battery_current(P, w, Tm, I))
+                        continue;
+                    const float dxi = __fdiv_rn(__fmul_rn(rec.dt, I), P.cap);
+                    int d;
+                    float f;
+                    snap_split(__fdiv_rn(-dxi, P.h_xi), d, f);
+                    const bool in4 = d >= -2 && d <= 1;
+                    if (bucket < 4 ? (d != bucket - 2) : in4)
+                        continue;
+                    const float mf = fuel_rate(P, w, Te);
+                    const float cost = __fmul_rn(__fadd_rn(__fmul_rn(P.gamma, mf), one_m_gamma), rec.dt);
+                    const int u = (ie * P.n_tm + im) * P.n_b + b;
+                    const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(d & 0xffff) << 16);
+                    spl_row[pos++] = make_float4(cost, __fsub_rn(1.f, f), f, __uint_as_float(bits));
+                    ++cnt;
+                }
+                if (bucket < 4)
+                    E.nb[bucket] = cnt;
+                else
+                    E.n_other = cnt;
+            }
+            ent_row[ent_idx] = E;
+        }
+        ent_carry += ent_tot;
+        spl_carry += spl_tot;
+    }
+    if (threadIdx.x == 0) {
+        sc.row_cnt[2 * i] = ent_carry;
+        sc.row_cnt[2 * i + 1] = spl_carry;
+        if (sc.stats) {
+            atomicAdd(sc.stats, (unsigned long long)spl_carry);
+            atomicAdd(sc.stats + 1, (unsigned long long)ent_carry);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fill(float *p, size_t n, float val, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    if (blocks < 1)
+        blocks = 1;
+    fill_kernel<<<blocks, 256, 0, s>>>(p, n, val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_terminal(const DevParams *dP, const DevParams &hP, float *VN, cudaStream_t s)
+{
+    int total = hP.n_v * hP.n_xi * hP.n_t;
+    int blocks = (total + 255) / 256;
+    terminal_kernel<<<blocks, 256, 0, s>>>(dP, VN);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
+                              cudaStream_t s)
+{
+    precompute_kernel<<<hP.n_v, 256, 0, s>>>(dP, tb, k, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float *padded, cudaStream_t s)
+{
+    int total = hP.n_v * hP.n_xi * hP.n_t;
+    pad_from_dense_kernel<<<(total + 255) / 256, 256, 0, s>>>(hP, dense, padded);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_from_pad(const DevParams &hP, const float *padded, float *dense, cudaStream_t s)
+{
+    int total = hP.n_v * hP.n_xi * hP.n_t;
+    dense_from_pad_kernel<<<(total + 255) / 256, 256, 0, s>>>(hP, padded, dense);
+    return cudaGetLastError();
+}
+
+}  // namespace ecodp

@@ -1,0 +1,218 @@
+// Forward rollout (trajectory extraction, the simulation step of Sec. V).
+//
+// One CTA walks the N stages from x0.  At every stage each thread evaluates
+// a strided subset of the controls at the continuous state: the one-step
+// model (Eq. 2, 5a-5c), the constraints (Eq. 7, 8) and the trilinear
+// interpolation of J_{k+1} at the continuous successor; a block argmin
+// (lowest control index on ties) selects the control, which is applied.
+// Cumulative time, fuel and cost are summed in FP64.
+#include <climits>
+
+#include "ecodp_internal.cuh"
+
+namespace ecodp {
+
+namespace {
+
+__device__ __forceinline__ bool locate_cont(float x, float lo, float h, int n, int &i, float &f)
+{
+    float q = __fdiv_rn(__fsub_rn(x, lo), h);
+    float top = (float)(n - 1);
+    if (q < -SNAP || q > top + SNAP)
+        return false;
+    q = fminf(fmaxf(q, 0.f), top);
+    snap_split(q, i, f);
+    if (i >= n - 1) {
+        i = n - 2;
+        f = 1.f;
+    }
+    return true;
+}
+
+// Trilinear interpolation of the padded value array at a continuous point.
+__device__ float interp_cont(const DevParams &P, const float *__restrict__ Vn, float v, float xi, float t)
+{
+    int iv, ix, it;
+    float fv, fx, ft;
+    if (!locate_cont(v, P.v_lo, P.h_v, P.n_v, iv, fv) || !locate_cont(xi, P.xi_lo, P.h_xi, P.n_xi, ix, fx) ||
+        !locate_cont(t, P.t_lo, P.h_t, P.n_t, it, ft))
+        return V_BIG;
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        float wa = a ? fv : __fsub_rn(1.f, fv);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            float wb = b ? fx : __fsub_rn(1.f, fx);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float wc = c ? ft : __fsub_rn(1.f, ft);
+                float val = Vn[((size_t)(iv + a) * P.xi_rows + (ix + b + 1)) * P.ld_t + (it + c)];
+                acc = __fmaf_rn(__fmul_rn(__fmul_rn(wa, wb), wc), val, acc);
+            }
+        }
+    }
+    return acc;
+}
+
+struct Step {
+    float v1, xi1, dt, wait, mf, cost;
+};
+
+// One model step from a continuous state; false if infeasible.
+__device__ bool model_step(const DevParams &P, const StageTables &tb, int k, float v, float xi, float t, int u,
+                           Step &s)
+{
+    int ie, im, b;
+    decode_u(P, u, ie, im, b);
+    const float Te = node_val(P.te_lo, P.te_span, ie, P.n_te);
+    const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
+    const float p = tb.grade[k];
+    const float sq = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(p, p)));
+    const float F_road = road_load(P, v, __fdiv_rn(p, sq), __fdiv_rn(1.f, sq));
+    const int nl = tb.light_of_node[k + 1];
+    float v1, dt;
+    if (!speed_step(P, v, F_road, __fadd_rn(Te, Tm), b, nl >= 0, v1, dt))
+        return false;
+    float wait = 0.f;
+    const int lk = tb.light_of_node[k];
+    if (lk >= 0 && v == 0.f) {
+        float ph = phase_pos(t, tb.offset[lk], tb.cycle[lk]);
+        if (ph < tb.red[lk])
+            wait = __fsub_rn(tb.red[lk], ph);
+    }
+    const float t1 = __fadd_rn(__fadd_rn(t, wait), dt);
+    if (nl >= 0 && v1 > 0.f && phase_pos(t1, tb.offset[nl], tb.cycle[nl]) < tb.red[nl])
+        return false;
+    const float w = __fmul_rn(v, P.ratio);
+    float I;
+    if (!battery_current(P, w, Tm, I))
+        return false;
+    const float mf = fuel_rate(P, w, Te);
+    const float one_m_gamma = __fsub_rn(1.f, P.gamma);
+    s.v1 = v1;
+    s.xi1 = __fsub_rn(xi, __fdiv_rn(__fmul_rn(dt, I), P.cap));
+    s.dt = dt;
+    s.wait = wait;
+    s.mf = mf;
+    s.cost = __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(P.gamma, mf), one_m_gamma), dt), __fmul_rn(one_m_gamma, wait));
+    return true;
+}
+
+constexpr int ROLL_THREADS = 512;
+
+__global__ void __launch_bounds__(ROLL_THREADS) rollout_kernel(const DevParams *__restrict__ dP, StageTables tb,
+                                                               const float *__restrict__ Vall, size_t stage_elems,
+                                                               double v0, double xi0, double t0,
+                                                               double *__restrict__ out, int *__restrict__ out_u)
+{
+    __shared__ DevParams P;
+    __shared__ float s_v, s_xi;
+    __shared__ double s_t, s_fuel, s_J;
+    __shared__ float red_F[ROLL_THREADS / 32];
+    __shared__ int red_u[ROLL_THREADS / 32];
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        P = *dP;
+        s_v = (float)v0;
+        s_xi = (float)xi0;
+        s_t = t0;
+        s_fuel = 0.0;
+        s_J = 0.0;
+        s_fail = -1;
+    }
+    __syncthreads();
+    const int N = P.N;
+    double *traj = out;
+    double *o_dt = out + 3 * (N + 1);
+    double *o_wait = o_dt + N;
+    double *o_fuel = o_wait + N;
+    double *o_tot = o_fuel + N;
+    if (threadIdx.x == 0) {
+        traj[0] = s_v;
+        traj[1] = s_xi;
+        traj[2] = s_t;
+    }
+    for (int k = 0; k < N; ++k) {
+        const float v = s_v, xi = s_xi, t = (float)s_t;
+        const float *Vn = Vall + (size_t)(k + 1) * stage_elems;
+        float bF = __int_as_float(0x7f800000);
+        int bu = INT_MAX;
+        for (int u = threadIdx.x; u < P.n_u; u += blockDim.x) {
+            Step s;
+            if (!model_step(P, tb, k, v, xi, t, u, s))
+                continue;
+            float F = __fadd_rn(s.cost, interp_cont(P, Vn, s.v1, s.xi1, __fadd_rn(__fadd_rn(t, s.wait), s.dt)));
+            if (F < V_FEAS_MAX && (F < bF || (F == bF && u < bu))) {
+                bF = F;
+                bu = u;
+            }
+        }
+        // block argmin on (F, u)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            float oF = __shfl_down_sync(0xffffffffu, bF, off);
+            int ou = __shfl_down_sync(0xffffffffu, bu, off);
+            if (oF < bF || (oF == bF && ou < bu)) {
+                bF = oF;
+                bu = ou;
+            }
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+            red_F[warp] = bF;
+            red_u[warp] = bu;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                if (red_F[w] < bF || (red_F[w] == bF && red_u[w] < bu)) {
+                    bF = red_F[w];
+                    bu = red_u[w];
+                }
+            }
+            if (bu == INT_MAX) {
+                s_fail = k;
+            } else {
+                Step s;
+                model_step(P, tb, k, v, xi, t, bu, s);
+                out_u[k] = bu;
+                o_dt[k] = s.dt;
+                o_wait[k] = s.wait;
+                const double fk = (double)s.mf * (double)s.dt;
+                o_fuel[k] = fk;
+                s_fuel += fk;
+                s_J += (double)s.cost;
+                s_t += (double)s.wait + (double)s.dt;
+                s_v = s.v1;
+                s_xi = s.xi1;
+                traj[3 * (k + 1) + 0] = s.v1;
+                traj[3 * (k + 1) + 1] = s.xi1;
+                traj[3 * (k + 1) + 2] = s_t;
+            }
+        }
+        __syncthreads();
+        if (s_fail >= 0)
+            break;
+    }
+    if (threadIdx.x == 0) {
+        o_tot[0] = s_fuel;
+        o_tot[1] = s_t - t0;
+        o_tot[2] = s_fail >= 0 ? __longlong_as_double(0x7ff0000000000000LL)
+                               : s_J + (double)terminal_cost(P, s_v, s_xi);
+        o_tot[3] = (double)s_fail;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
+                           size_t stage_elems, double v0, double xi0, double t0, double *out, int *out_u,
+                           cudaStream_t s)
+{
+    (void)hP;
+    rollout_kernel<<<1, ROLL_THREADS, 0, s>>>(dP, tb, Vall, stage_elems, v0, xi0, t0, out, out_u);
+    return cudaGetLastError();
+}
+
+}  // namespace ecodp

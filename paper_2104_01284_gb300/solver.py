@@ -1,0 +1,192 @@
+"""PyTorch-facing wrapper of the ecodp C ABI.
+
+PyTorch provides device memory (the caching allocator, through the C ABI's
+allocator callbacks) and streams; all computation happens in libecodp.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import native as N
+
+_INF = float("inf")
+
+
+def make_desc(p):
+    """Marshal a problems.Problem into a dp_problem_desc.  Returns (desc,
+    keepalive) -- keep the second object alive while the desc is in use."""
+    keep = []
+
+    def arr(x, dtype, ctype):
+        a = np.ascontiguousarray(x, dtype=dtype)
+        if a.size == 0:
+            a = np.zeros(1, dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data_as(C.POINTER(ctype))
+
+    d = N.ProblemDesc()
+    d.n_stages = int(p.n_stages)
+    d.ds = float(p.ds)
+    d.grade = arr(p.grade, np.float64, C.c_double)
+    for f in ("v_lo", "v_hi", "soc_lo", "soc_hi", "t_lo", "t_hi", "te_lo", "te_hi", "tm_lo", "tm_hi",
+              "brake_decel", "a_min", "a_max", "mass", "cda", "crr", "rho", "g", "r_wheel", "gear",
+              "eta_motor", "voc", "r0", "capacity_As", "fuel_scale", "gamma", "soc_ref", "w_soc", "v_ref",
+              "w_v"):
+        setattr(d, f, float(getattr(p, f)))
+    for f in ("n_v", "n_soc", "n_t", "n_te", "n_tm", "n_brake"):
+        setattr(d, f, int(getattr(p, f)))
+    for q in range(6):
+        d.fuel_coef[q] = float(p.fuel_coef[q])
+    d.n_lights = int(len(p.light_stage))
+    d.light_stage = arr(p.light_stage, np.int32, C.c_int32)
+    d.cycle = arr(p.cycle, np.float64, C.c_double)
+    d.red = arr(p.red, np.float64, C.c_double)
+    d.offset = arr(p.offset, np.float64, C.c_double)
+    return d, keep
+
+
+class TorchAllocator:
+    """dp_allocator backed by PyTorch's CUDA caching allocator."""
+
+    def __init__(self, device: torch.device):
+        self.device = device.index if device.index is not None else torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0)
+            except Exception:  # reported to the library as NULL -> DP_ERR_OOM
+                return None
+
+        def _free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc = N.ALLOC_FN(_alloc)
+        self._free = N.FREE_FN(_free)
+        self.struct = N.Allocator(self._alloc, self._free, None)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class EcoDP:
+    """One receding-horizon DP problem resident on a GPU.
+
+    >>> dp = EcoDP(problems.config1())
+    >>> dp.solve()                # backward sweep (Eq. 9), asynchronous
+    >>> traj = dp.rollout()       # optimal trajectory from p.x0
+    """
+
+    def __init__(self, p, device=None, stream=None, use_torch_allocator: bool = True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("EcoDP needs a CUDA device; the solver has no CPU fallback")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.p = p
+        self._alloc = TorchAllocator(self.device) if use_torch_allocator else None
+        desc, keep = make_desc(p)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            s = _stream_handle(stream)
+            N.check(N.dp_problem_create(C.byref(desc), C.byref(self._alloc.struct) if self._alloc else None,
+                                        s, C.byref(h)), "dp_problem_create")
+        del keep
+        self.h = h
+        sz = (C.c_int32 * 5)()
+        N.check(N.dp_problem_sizes(self.h, sz), "dp_problem_sizes")
+        self.n_stages, self.n_v, self.n_soc, self.n_t, self.n_controls = list(sz)
+        self.shape = (self.n_v, self.n_soc, self.n_t)
+
+    # -- lifecycle ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            with torch.cuda.device(self.device):
+                N.check(N.dp_problem_destroy(self.h), "dp_problem_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def update(self, p, stream=None):
+        """Replace grade, lights and model constants (same sizes)."""
+        desc, keep = make_desc(p)
+        N.check(N.dp_problem_update(self.h, C.byref(desc), _stream_handle(stream)), "dp_problem_update")
+        del keep
+        self.p = p
+
+    def set_variant(self, variant: str):
+        N.check(N.dp_set_kernel_variant(self.h, {"direct": 0, "tiled": 1}[variant]), "dp_set_kernel_variant")
+
+    # -- compute ------------------------------------------------------------
+    def solve(self, stream=None):
+        with torch.cuda.device(self.device):
+            N.check(N.dp_solve_backward(self.h, _stream_handle(stream)), "dp_solve_backward")
+
+    def profile_sweep(self, stream=None):
+        """One backward sweep with per-kernel CUDA events (direct launches);
+        returns milliseconds {terminal, precompute, bellman, sweep}."""
+        ms = (C.c_float * 4)()
+        with torch.cuda.device(self.device):
+            N.check(N.dp_profile_sweep(self.h, _stream_handle(stream), ms), "dp_profile_sweep")
+        return dict(terminal=ms[0], precompute=ms[1], bellman=ms[2], sweep=ms[3])
+
+    def sweep_stats(self, stream=None):
+        """Counters of the last sweep: effective state x control evaluations,
+        state x class pairs, and the bytes of one update / one rollout copy."""
+        out = (C.c_int64 * 4)()
+        N.check(N.dp_sweep_stats(self.h, out, _stream_handle(stream)), "dp_sweep_stats")
+        return dict(effective_evals=out[0], class_evals=out[1], h2d_update_bytes=out[2], d2h_rollout_bytes=out[3])
+
+    def value(self, k: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        N.check(N.dp_get_value(self.h, int(k), out.data_ptr(), 0, _stream_handle(stream)), "dp_get_value")
+        return out
+
+    def policy(self, k: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.int16, device=self.device)
+        N.check(N.dp_get_policy(self.h, int(k), out.data_ptr(), 0, _stream_handle(stream)), "dp_get_policy")
+        return out
+
+    def solve_stage(self, k: int, v_next, stream=None):
+        """One Bellman stage from a given J_{k+1} (float32 [n_v, n_soc, n_t],
+        +inf = infeasible, on the device).  Returns (J_k, pi_k) tensors."""
+        vn = torch.as_tensor(v_next, dtype=torch.float32, device=self.device).contiguous()
+        assert tuple(vn.shape) == self.shape
+        vo = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        po = torch.empty(self.shape, dtype=torch.int16, device=self.device)
+        with torch.cuda.device(self.device):
+            N.check(N.dp_solve_stage(self.h, int(k), vn.data_ptr(), 0, vo.data_ptr(), po.data_ptr(), 0,
+                                     _stream_handle(stream)), "dp_solve_stage")
+        return vo, po
+
+    def rollout(self, x0=None, stream=None, raise_infeasible: bool = True):
+        """Forward rollout from x0 (default p.x0); returns numpy arrays."""
+        n = self.n_stages
+        x = np.array(self.p.x0 if x0 is None else x0, dtype=np.float64)
+        bufs = dict(v=np.empty(n + 1), soc=np.empty(n + 1), t=np.empty(n + 1), u=np.empty(n, np.int32),
+                    dt=np.empty(n), wait=np.empty(n), fuel=np.empty(n))
+        tr = N.Trajectory()
+        for key, a in bufs.items():
+            ct = C.c_int32 if a.dtype == np.int32 else C.c_double
+            setattr(tr, key, a.ctypes.data_as(C.POINTER(ct)))
+        with torch.cuda.device(self.device):
+            st = N.dp_rollout(self.h, x.ctypes.data_as(C.POINTER(C.c_double)), C.byref(tr), _stream_handle(stream))
+        if st != N.DP_OK and (raise_infeasible or st != N.DP_ERR_INFEASIBLE):
+            N.check(st, "dp_rollout")
+        out = dict(bufs)
+        out["traj"] = np.stack([bufs["v"], bufs["soc"], bufs["t"]], axis=1)
+        out.update(fuel_g=tr.fuel_g, time_s=tr.time_s, J=tr.J, fail_stage=tr.fail_stage, status=st)
+        return out
