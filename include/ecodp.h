@@ -155,6 +155,33 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
  * control (traj->fail_stage tells which); DP_ERR_NOT_SOLVED before a solve. */
 dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream);
 
+/* One stage of the recursion, like dp_solve_stage, for callers that cannot
+ * allocate GPU memory.  The paper has no counterpart; this entry point exists
+ * for integrations whose memory is fixed after start-up: a controller task
+ * that runs under a hard real-time budget (cudaMalloc and cudaFree may block
+ * and synchronise the whole device), or code embedded in a host framework
+ * that owns every device allocation and forbids others.  Such callers cannot
+ * create a dp_problem (it allocates), so this call takes the descriptor
+ * directly and allocates nothing: its working memory is one static device
+ * array of about 12 MB built into the library, present on every GPU that
+ * loads it until the process exits.
+ *   desc:    the problem (host memory); only stage k's grade and lights are used
+ *   v_next:  J_{k+1}, float32 [n_v][n_soc][n_t] in DEVICE memory, +INFINITY =
+ *            infeasible
+ *   v_out:   J_k, same layout, DEVICE memory (caller-owned)
+ *   pi_out:  pi_k, int16 same shape, DEVICE memory (caller-owned)
+ * Results equal those of dp_solve_stage on the same inputs.  Limits: n_v <= 64,
+ * n_soc <= 64, n_t <= 255, at most 2048 controls and 256 torque classes;
+ * larger problems get DP_ERR_INVALID_ARG.  Asynchronous on stream.  The first
+ * call on each device looks up the array's device address (a set-up step);
+ * make that first call before capturing any stream into a CUDA graph.  Every
+ * call on a device shares that device's one array, so calls whose GPU work
+ * can overlap (issued on different streams or from different host threads)
+ * race and corrupt each other's results: order them on one stream.  Each
+ * call re-initialises what it reads from the array. */
+dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t k, const float *v_next, float *v_out,
+                                int16_t *pi_out, void *stream);
+
 /* Human-readable name of a status, and the last error message of the
  * calling thread (empty string if none). */
 const char *dp_status_string(dp_status s);

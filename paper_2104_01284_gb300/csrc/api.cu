@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -663,3 +665,126 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single stage (dp_solve_stage_static).
+//
+// Its working memory is one file-scope device array, sized for the limits
+// below and resident on every GPU that loads this library until the process
+// exits.  Host code must not pass the array's name to a kernel (on the host
+// it only stands in for the symbol); each device's address is looked up once
+// with cudaGetSymbolAddress and cached.
+
+namespace {
+
+constexpr int STATIC_MAX_V = 64, STATIC_MAX_SOC = 64, STATIC_MAX_T = 255, STATIC_MAX_U = 2048,
+              STATIC_MAX_CLS = 256;
+constexpr size_t STATIC_LD_T = 256;  // round_up(STATIC_MAX_T + 1, 4)
+constexpr size_t STATIC_PAD_ELEMS = (size_t)STATIC_MAX_V * (STATIC_MAX_SOC + 2) * STATIC_LD_T;
+
+constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t ST_OFF_PARAMS = 0;
+constexpr size_t ST_OFF_TABLES = ST_OFF_PARAMS + a256(sizeof(DevParams));
+constexpr size_t ST_TABLE_BYTES = a256(4 * sizeof(float) + 2 * sizeof(int) + 6 * sizeof(float));
+constexpr size_t ST_OFF_CLS = ST_OFF_TABLES + ST_TABLE_BYTES;
+constexpr size_t ST_OFF_ENT = ST_OFF_CLS + a256((size_t)STATIC_MAX_V * STATIC_MAX_CLS * sizeof(ClassRec));
+constexpr size_t ST_OFF_ROWCNT = ST_OFF_ENT + a256((size_t)STATIC_MAX_V * STATIC_MAX_CLS * sizeof(ClassEntry));
+constexpr size_t ST_OFF_SPL = ST_OFF_ROWCNT + a256((size_t)STATIC_MAX_V * 2 * sizeof(int));
+constexpr size_t ST_OFF_PAD_IN = ST_OFF_SPL + a256((size_t)STATIC_MAX_V * STATIC_MAX_U * sizeof(float4));
+constexpr size_t ST_OFF_PAD_OUT = ST_OFF_PAD_IN + a256(STATIC_PAD_ELEMS * sizeof(float));
+constexpr size_t ST_BYTES = ST_OFF_PAD_OUT + a256(STATIC_PAD_ELEMS * sizeof(float));  // about 12 MB
+
+__device__ __align__(256) unsigned char g_stage_scratch[ST_BYTES];
+
+std::mutex g_static_mu;
+void *g_static_addr[128] = {};
+
+// Device address of g_stage_scratch on the current device (set-up on first use).
+dp_status static_scratch(unsigned char **out)
+{
+    int dev = -1;
+    DP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128)
+        return fail(DP_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_stage_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(DP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_static_addr[dev] = ptr;
+    }
+    *out = (unsigned char *)g_static_addr[dev];
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t k, const float *v_next, float *v_out,
+                                           int16_t *pi_out, void *stream)
+{
+    dp_status st = validate(desc);
+    if (st != DP_OK)
+        return st;
+    if (!v_next || !v_out || !pi_out)
+        return fail(DP_ERR_INVALID_ARG, "v_next, v_out and pi_out must be device pointers");
+    if (k < 0 || k >= desc->n_stages)
+        return fail(DP_ERR_INVALID_ARG, "stage out of range");
+    DevParams P;
+    fill_params(desc, P);
+    if (P.n_v > STATIC_MAX_V || P.n_xi > STATIC_MAX_SOC || P.n_t > STATIC_MAX_T || P.n_u > STATIC_MAX_U ||
+        P.n_cls > STATIC_MAX_CLS)
+        return fail(DP_ERR_INVALID_ARG,
+                    "dp_solve_stage_static supports at most 64 speeds, 64 SoC points, 255 times, 2048 controls and "
+                    "256 torque classes; use dp_solve_stage for larger problems");
+    unsigned char *base = nullptr;
+    st = static_scratch(&base);
+    if (st != DP_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // the stage's own tables, re-indexed as stage 0 of a one-stage problem:
+    // grade, light index at the departure node (0) and at the arrival node (1)
+    struct {
+        float grade[4];
+        int lon[2];
+        float cyc[2], red[2], off[2];
+    } tbl = {};
+    tbl.grade[0] = (float)desc->grade[k];
+    tbl.lon[0] = tbl.lon[1] = -1;
+    tbl.cyc[0] = tbl.cyc[1] = 1.f;
+    for (int q = 0; q < desc->n_lights; ++q) {
+        for (int side = 0; side < 2; ++side) {
+            if (desc->light_stage[q] == k + side) {
+                tbl.lon[side] = side;
+                tbl.cyc[side] = (float)desc->cycle[q];
+                tbl.red[side] = (float)desc->red[q];
+                tbl.off[side] = (float)desc->offset[q];
+            }
+        }
+    }
+    static_assert(sizeof(tbl) <= ST_TABLE_BYTES, "table block");
+    unsigned char *tb_dev = base + ST_OFF_TABLES;
+    DevParams *dP = (DevParams *)(base + ST_OFF_PARAMS);
+    StageTables tb{(const float *)(tb_dev + offsetof(decltype(tbl), grade)),
+                   (const int *)(tb_dev + offsetof(decltype(tbl), lon)),
+                   (const float *)(tb_dev + offsetof(decltype(tbl), cyc)),
+                   (const float *)(tb_dev + offsetof(decltype(tbl), red)),
+                   (const float *)(tb_dev + offsetof(decltype(tbl), off))};
+    StageScratch sc{(ClassRec *)(base + ST_OFF_CLS), (ClassEntry *)(base + ST_OFF_ENT), (int *)(base + ST_OFF_ROWCNT),
+                    (float4 *)(base + ST_OFF_SPL), nullptr};
+    float *pad_in = (float *)(base + ST_OFF_PAD_IN);
+    float *pad_out = (float *)(base + ST_OFF_PAD_OUT);
+    const size_t pad_elems = (size_t)P.n_v * P.xi_rows * P.ld_t;
+
+    DP_CUDA(cudaMemcpyAsync(dP, &P, sizeof P, cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(tb_dev, &tbl, sizeof tbl, cudaMemcpyHostToDevice, s));
+    // the padding of J_{k+1} must read as infeasible: refill it every call,
+    // since the array keeps whatever the previous call left there
+    DP_CUDA(launch_fill(pad_in, pad_elems, V_BIG, s));
+    DP_CUDA(launch_pad_from_dense(P, v_next, pad_in, s));
+    DP_CUDA(launch_precompute(dP, P, tb, 0, sc, s));
+    DP_CUDA(launch_bellman(dP, P, tb, 0, sc, pad_in, pad_out, pi_out, 1, s));
+    DP_CUDA(launch_dense_from_pad(P, pad_out, v_out, s));
+    return DP_OK;
+}

@@ -103,3 +103,7 @@ class DPError(RuntimeError):
 def check(status: int, where: str):
     if status != DP_OK:
         raise DPError(status, where)
+
+# allocation-free single stage (static device working memory)
+dp_solve_stage_static = _sig("dp_solve_stage_static", C.POINTER(ProblemDesc), C.c_int32, vp, vp, vp, vp)
+EXPORTED.append("dp_solve_stage_static")
