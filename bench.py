@@ -212,7 +212,7 @@ def run_ours(args):
     p = workload(args.seed)
     stream = torch.cuda.Stream(dev)
     dp = EcoDP(p, device=dev, stream=stream)
-    launches_per_step = 1 + 2 * p.n_stages + 1  # terminal, N x (precompute, Bellman), rollout
+    launches_per_step = 1 + 1 + p.n_stages + 1  # terminal, precompute (all stages), N x Bellman, rollout
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
@@ -267,7 +267,8 @@ def run_ours(args):
                 "bellman_ms_per_launch": 1e3 * per_launch_s,
                 "share_of_sweep": bell_ms / sweep_ms if sweep_ms > 0 else None,
                 "precompute_ms_per_launch": pre_ms / p.n_stages,
-                "effective_evals_per_s": stats["effective_evals"] / (bell_ms / 1e3)}
+                "effective_evals_per_s": stats["effective_evals"] / (bell_ms / 1e3),
+                "tie_states": stats["tie_states"], "argmin_states": stats["argmin_states"]}
 
     # end to end through the public API with host buffers: upload the
     # problem tables, solve, read the trajectory back, every step

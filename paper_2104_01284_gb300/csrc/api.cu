@@ -16,7 +16,7 @@
 using namespace ecodp;
 
 namespace ecodp {
-size_t bellman_smem_bytes(const DevParams &hP, bool smem_splits);
+size_t bellman_smem_bytes(const DevParams &hP);
 }
 
 namespace {
@@ -57,7 +57,7 @@ struct dp_problem {
     ClassRec *d_cls = nullptr;
     ClassEntry *d_ent = nullptr;
     int *d_rowcnt = nullptr;
-    float4 *d_spl = nullptr;
+    SplitRec *d_spl = nullptr;
     float *d_pad_in = nullptr, *d_pad_out = nullptr, *d_dense = nullptr;
     int16_t *d_pi_tmp = nullptr;
     double *d_roll = nullptr;
@@ -104,6 +104,8 @@ dp_status validate(const dp_problem_desc *d)
         return fail(DP_ERR_INVALID_ARG, "control grids need n_te, n_tm >= 1 and n_brake in {1, 2}");
     if ((long long)d->n_te * d->n_tm * d->n_brake > 32767)
         return fail(DP_ERR_INVALID_ARG, "at most 32767 controls (int16 policy)");
+    if ((long long)d->n_te * d->n_tm * d->n_brake > MAX_CONTROLS)
+        return fail(DP_ERR_INVALID_ARG, "at most 8192 controls (per-control tables live in shared memory)");
     if (!d->grade)
         return fail(DP_ERR_INVALID_ARG, "grade is NULL");
     if (!finite_all({d->ds, d->v_lo, d->v_hi, d->soc_lo, d->soc_hi, d->t_lo, d->t_hi, d->te_lo, d->te_hi,
@@ -164,7 +166,7 @@ void fill_params(const dp_problem_desc *d, DevParams &P)
     bool same_step = (d->n_te == 1 || d->n_tm == 1) ? true : (he == hm);
     P.class_sum = same_step ? 1 : 0;
     P.n_cls = (same_step ? (d->n_te + d->n_tm - 1) : (d->n_te * d->n_tm)) * d->n_brake;
-    P.ld_t = round_up(d->n_t + 1, 4);
+    P.ld_t = round_up(d->n_t + 2, 4);
     P.xi_rows = d->n_soc + 2;
     P.n_lights = d->n_lights;
     P.v_lo = f32(d->v_lo);
@@ -282,17 +284,17 @@ dp_status upload_tables(dp_problem *p, cudaStream_t s)
     return DP_OK;
 }
 
-// The backward sweep's launches (terminal values, then per stage the
-// precompute and Bellman kernels).
+// The backward sweep's launches: terminal values, the precompute tables of
+// every stage (they depend on the route, not on J), then the N Bellman
+// stages in backward order.
 dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 {
-    DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 2 * sizeof(unsigned long long), s));
+    DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s));
     DP_CUDA(launch_terminal(p->dP, p->hP, p->V(p->N), s));
-    for (int k = p->N - 1; k >= 0; --k) {
-        DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, p->scratch(), s));
+    DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, p->N, p->scratch(), s));
+    for (int k = p->N - 1; k >= 0; --k)
         DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->V(k + 1), p->V(k), p->pi(k),
                                p->variant, s));
-    }
     return DP_OK;
 }
 
@@ -366,17 +368,23 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, p->h_off.size(), &p->d_off));
     TRY(dev_alloc_n(p, p->stage_elems * (size_t)(p->N + 1), &p->d_V));
     TRY(dev_alloc_n(p, p->pi_elems * (size_t)p->N, &p->d_pi));
-    TRY(dev_alloc_n(p, (size_t)P.n_v * P.n_cls, &p->d_cls));
-    TRY(dev_alloc_n(p, (size_t)P.n_v * P.n_cls, &p->d_ent));
-    TRY(dev_alloc_n(p, (size_t)P.n_v * 2, &p->d_rowcnt));
-    TRY(dev_alloc_n(p, (size_t)P.n_v * P.n_u, &p->d_spl));
+    if (P.n_cls > MAX_CLASSES) {
+        release(p);
+        delete p;
+        return fail(DP_ERR_INVALID_ARG, "at most 4095 torque classes (unequal torque steps give one per control)");
+    }
+    const size_t rows = (size_t)P.N * P.n_v;  // one table slot per stage
+    TRY(dev_alloc_n(p, rows * P.n_cls, &p->d_cls));
+    TRY(dev_alloc_n(p, rows * P.n_cls, &p->d_ent));
+    TRY(dev_alloc_n(p, rows * 2, &p->d_rowcnt));
+    TRY(dev_alloc_n(p, rows * P.n_u, &p->d_spl));
     TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_in));
     TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_out));
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_dense));
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_pi_tmp));
     TRY(dev_alloc_n(p, (size_t)(3 * (P.N + 1) + 3 * P.N + 4), &p->d_roll));
     TRY(dev_alloc_n(p, (size_t)P.N, &p->d_roll_u));
-    TRY(dev_alloc_n(p, (size_t)2, &p->d_stats));
+    TRY(dev_alloc_n(p, (size_t)4, &p->d_stats));
     TRY(upload_tables(p, p->create_stream));
     auto cuda_try = [&](cudaError_t e, const char *what) -> dp_status {
         if (e != cudaSuccess)
@@ -388,7 +396,7 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
-    size_t smem = bellman_smem_bytes(P, bellman_smem_bytes(P, true) <= 160 * 1024);
+    size_t smem = bellman_smem_bytes(P);
     if (smem > 227 * 1024) {
         release(p);
         delete p;
@@ -442,13 +450,13 @@ dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5])
     return DP_OK;
 }
 
-dp_status dp_sweep_stats(dp_problem_t p, int64_t out[4], void *stream)
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[6], void *stream)
 {
     if (!p || !out)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!p->solved)
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};
     cudaStream_t s = (cudaStream_t)stream;
     DP_CUDA(cudaMemcpyAsync(h, p->d_stats, sizeof h, cudaMemcpyDeviceToHost, s));
     DP_CUDA(cudaStreamSynchronize(s));
@@ -458,6 +466,8 @@ dp_status dp_sweep_stats(dp_problem_t p, int64_t out[4], void *stream)
     out[2] = (int64_t)(sizeof(DevParams) + p->h_grade.size() * sizeof(float) + p->h_lon.size() * sizeof(int) +
                        3 * p->h_cyc.size() * sizeof(float));
     out[3] = (int64_t)((3 * (p->N + 1) + 3 * p->N + 4) * sizeof(double) + p->N * sizeof(int));
+    out[4] = (int64_t)h[2];
+    out[5] = (int64_t)h[3];
     return DP_OK;
 }
 
@@ -516,33 +526,32 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int N = p->N;
-    std::vector<cudaEvent_t> ev(2 * N + 2, nullptr);
+    std::vector<cudaEvent_t> ev(N + 3, nullptr);
     for (auto &e : ev)
         DP_CUDA(cudaEventCreate(&e));
     dp_status st = DP_OK;
     auto run = [&]() -> dp_status {
-        DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 2 * sizeof(unsigned long long), s));
+        DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s));
         DP_CUDA(cudaEventRecord(ev[0], s));
         DP_CUDA(launch_terminal(p->dP, p->hP, p->V(N), s));
         DP_CUDA(cudaEventRecord(ev[1], s));
-        for (int k = N - 1, q = 1; k >= 0; --k, q += 2) {
-            DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, p->scratch(), s));
-            DP_CUDA(cudaEventRecord(ev[q + 1], s));
+        DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, N, p->scratch(), s));
+        DP_CUDA(cudaEventRecord(ev[2], s));
+        for (int k = N - 1, q = 3; k >= 0; --k, ++q) {
             DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->V(k + 1), p->V(k), p->pi(k),
                                    p->variant, s));
-            DP_CUDA(cudaEventRecord(ev[q + 2], s));
+            DP_CUDA(cudaEventRecord(ev[q], s));
         }
-        DP_CUDA(cudaEventSynchronize(ev[2 * N + 1]));
+        DP_CUDA(cudaEventSynchronize(ev[N + 2]));
         float t = 0.f, pre = 0.f, bell = 0.f, all = 0.f;
         DP_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
-        for (int q = 1; q < 2 * N + 1; q += 2) {
-            float a = 0.f, b = 0.f;
-            DP_CUDA(cudaEventElapsedTime(&a, ev[q], ev[q + 1]));
-            DP_CUDA(cudaEventElapsedTime(&b, ev[q + 1], ev[q + 2]));
-            pre += a;
+        DP_CUDA(cudaEventElapsedTime(&pre, ev[1], ev[2]));
+        for (int q = 3; q < N + 3; ++q) {
+            float b = 0.f;
+            DP_CUDA(cudaEventElapsedTime(&b, ev[q - 1], ev[q]));
             bell += b;
         }
-        DP_CUDA(cudaEventElapsedTime(&all, ev[0], ev[2 * N + 1]));
+        DP_CUDA(cudaEventElapsedTime(&all, ev[0], ev[N + 2]));
         ms[0] = t;
         ms[1] = pre;
         ms[2] = bell;
@@ -605,7 +614,7 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
     StageScratch sc = p->scratch();
     sc.stats = nullptr;
     DP_CUDA(launch_pad_from_dense(p->hP, p->d_dense, p->d_pad_in, s));
-    DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, sc, s));
+    DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), k, 1, sc, s));
     DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, sc, p->d_pad_in, p->d_pad_out, p->d_pi_tmp, p->variant, s));
     if (v_out) {
         DP_CUDA(launch_dense_from_pad(p->hP, p->d_pad_out, p->d_dense, s));
@@ -679,7 +688,7 @@ namespace {
 
 constexpr int STATIC_MAX_V = 64, STATIC_MAX_SOC = 64, STATIC_MAX_T = 255, STATIC_MAX_U = 2048,
               STATIC_MAX_CLS = 256;
-constexpr size_t STATIC_LD_T = 256;  // round_up(STATIC_MAX_T + 1, 4)
+constexpr size_t STATIC_LD_T = (STATIC_MAX_T + 2 + 3) / 4 * 4;  // the largest ld_t = round_up(n_t + 2, 4)
 constexpr size_t STATIC_PAD_ELEMS = (size_t)STATIC_MAX_V * (STATIC_MAX_SOC + 2) * STATIC_LD_T;
 
 constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -690,7 +699,7 @@ constexpr size_t ST_OFF_CLS = ST_OFF_TABLES + ST_TABLE_BYTES;
 constexpr size_t ST_OFF_ENT = ST_OFF_CLS + a256((size_t)STATIC_MAX_V * STATIC_MAX_CLS * sizeof(ClassRec));
 constexpr size_t ST_OFF_ROWCNT = ST_OFF_ENT + a256((size_t)STATIC_MAX_V * STATIC_MAX_CLS * sizeof(ClassEntry));
 constexpr size_t ST_OFF_SPL = ST_OFF_ROWCNT + a256((size_t)STATIC_MAX_V * 2 * sizeof(int));
-constexpr size_t ST_OFF_PAD_IN = ST_OFF_SPL + a256((size_t)STATIC_MAX_V * STATIC_MAX_U * sizeof(float4));
+constexpr size_t ST_OFF_PAD_IN = ST_OFF_SPL + a256((size_t)STATIC_MAX_V * STATIC_MAX_U * sizeof(SplitRec));
 constexpr size_t ST_OFF_PAD_OUT = ST_OFF_PAD_IN + a256(STATIC_PAD_ELEMS * sizeof(float));
 constexpr size_t ST_BYTES = ST_OFF_PAD_OUT + a256(STATIC_PAD_ELEMS * sizeof(float));  // about 12 MB
 
@@ -772,7 +781,9 @@ extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t 
                    (const float *)(tb_dev + offsetof(decltype(tbl), red)),
                    (const float *)(tb_dev + offsetof(decltype(tbl), off))};
     StageScratch sc{(ClassRec *)(base + ST_OFF_CLS), (ClassEntry *)(base + ST_OFF_ENT), (int *)(base + ST_OFF_ROWCNT),
-                    (float4 *)(base + ST_OFF_SPL), nullptr};
+                    (SplitRec *)(base + ST_OFF_SPL), nullptr};
+    if (P.ld_t > (int)STATIC_LD_T || (size_t)P.n_v * P.xi_rows * P.ld_t > STATIC_PAD_ELEMS)
+        return fail(DP_ERR_INTERNAL, "static working memory layout too small");
     float *pad_in = (float *)(base + ST_OFF_PAD_IN);
     float *pad_out = (float *)(base + ST_OFF_PAD_OUT);
     const size_t pad_elems = (size_t)P.n_v * P.xi_rows * P.ld_t;
@@ -783,7 +794,7 @@ extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t 
     // since the array keeps whatever the previous call left there
     DP_CUDA(launch_fill(pad_in, pad_elems, V_BIG, s));
     DP_CUDA(launch_pad_from_dense(P, v_next, pad_in, s));
-    DP_CUDA(launch_precompute(dP, P, tb, 0, sc, s));
+    DP_CUDA(launch_precompute(dP, P, tb, 0, 1, sc, s));
     DP_CUDA(launch_bellman(dP, P, tb, 0, sc, pad_in, pad_out, pi_out, 1, s));
     DP_CUDA(launch_dense_from_pad(P, pad_out, v_out, s));
     return DP_OK;

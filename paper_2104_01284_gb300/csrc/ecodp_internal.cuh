@@ -7,13 +7,15 @@
 //   V   float [N+1][n_v][n_soc+2][ld_t]   value function of every stage.  Soc
 //       rows 0 and n_soc+1 and time columns >= n_t are padding that always
 //       holds V_BIG, so an interpolation corner that falls outside the grid
-//       reads an "infeasible" value without a branch.  ld_t = round_up(n_t+1,
-//       4) keeps every row 16-byte aligned.
+//       reads an "infeasible" value without a branch.  ld_t = round_up(n_t+2,
+//       4) keeps every row 16-byte aligned and leaves the column after the
+//       first padding column inside the row (a clamped lower time corner at
+//       n_t still has its upper neighbour there).
 //   pi  int16 [N][n_v][n_soc][n_t]        argmin control index, -1 infeasible.
-//   per-stage scratch (rewritten at every stage by the precompute kernel):
-//       ClassRec  [n_v][n_cls]  speed/time transition of every torque class
-//       ClassEntry[n_v][n_cls]  the feasible classes of each speed row
-//       float4    [n_v][n_u]    per-control record {cost, w0, w1, u|d}
+//   per-stage tables (written for every stage by the precompute kernel):
+//       ClassRec  [N][n_v][n_cls]  speed/time transition of every torque class
+//       ClassEntry[N][n_v][n_cls]  the feasible classes of each speed row
+//       SplitRec  [N][n_v][n_u]    per-control record (cost, SoC shift, weights, u)
 //
 // Infeasibility is carried as the finite sentinel V_BIG instead of +inf: an
 // interpolation weight of exactly 0 (a snapped fraction) then contributes
@@ -65,6 +67,14 @@ struct ClassRec {
     int st;     // floor(dt / h_t) after snapping
     float ft;   // snapped fraction of dt / h_t
     int pad;
+};
+
+// One feasible control: its stage cost c (Eq. 1/6), its SoC-axis shift d and
+// interpolation weights (w0, w1) of xi' = xi - dt I / C_nom (Eq. 5b), and its
+// index u, packed as bits = u | d << 16.  16 bytes: one vector load.
+struct __align__(16) SplitRec {
+    float c, w0, w1;
+    unsigned bits;
 };
 
 struct ClassEntry {
@@ -188,12 +198,15 @@ __device__ __forceinline__ float terminal_cost(const DevParams &P, float v, floa
     return __fadd_rn(__fmul_rn(P.w_soc, sh), __fmul_rn(P.w_v, __fmul_rn(dv, dv)));
 }
 
-// Bilinear blend of two speed rows at two time columns.
-__device__ __forceinline__ float g_blend(const float *__restrict__ r0, const float *__restrict__ r1, int ta, int tb,
-                                         float wv0, float wv1, float wt0, float wt1)
+// Bilinear blend of two speed rows (p0, p1 point at the lower time column,
+// the upper one follows it): the speed/time part of the trilinear
+// interpolation of J_{k+1}.  Every caller uses this one function so that
+// values are reproduced bit for bit.
+__device__ __forceinline__ float g_blend2(const float *__restrict__ p0, const float *__restrict__ p1, float wv0,
+                                          float wv1, float wt0, float wt1)
 {
-    float A = __fmaf_rn(wv1, __ldg(r1 + ta), __fmul_rn(wv0, __ldg(r0 + ta)));
-    float B = __fmaf_rn(wv1, __ldg(r1 + tb), __fmul_rn(wv0, __ldg(r0 + tb)));
+    float A = __fmaf_rn(wv1, __ldg(p1), __fmul_rn(wv0, __ldg(p0)));
+    float B = __fmaf_rn(wv1, __ldg(p1 + 1), __fmul_rn(wv0, __ldg(p0 + 1)));
     return __fmaf_rn(wt1, B, __fmul_rn(wt0, A));
 }
 
@@ -205,18 +218,29 @@ struct StageTables {
     const float *cycle, *red, *offset;
 };
 
+// Tables of the precompute kernel, one slot per stage k (slot k holds stage
+// k; a one-stage caller uses slot 0 with its tables re-indexed as stage 0).
 struct StageScratch {
-    ClassRec *cls;    // [n_v][n_cls]
-    ClassEntry *ent;  // [n_v][n_cls]
-    int *row_cnt;     // [n_v][2] feasible classes, splits
-    float4 *spl;      // [n_v][n_u]
-    unsigned long long *stats;  // [2] running totals: feasible (v, u) pairs, feasible (v, class) pairs
+    ClassRec *cls;    // [slots][n_v][n_cls]
+    ClassEntry *ent;  // [slots][n_v][n_cls]
+    int *row_cnt;     // [slots][n_v][2] feasible classes, splits
+    SplitRec *spl;    // [slots][n_v][n_u]
+    // [4] running totals (may be NULL): feasible (v, u) pairs, feasible
+    // (v, class) pairs, states whose minimum ties across classes, states
+    // whose argmin was recovered
+    unsigned long long *stats;
 };
+
+// Limits of the tiled path (validated at create): controls per problem and
+// torque classes (per-control and per-class tables live in shared memory).
+constexpr int MAX_CONTROLS = 8192;
+constexpr int MAX_CLASSES = 4095;
 
 cudaError_t launch_fill(float *p, size_t n, float val, cudaStream_t s);
 cudaError_t launch_terminal(const DevParams *dP, const DevParams &hP, float *VN, cudaStream_t s);
-cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
-                              cudaStream_t s);
+// Tables of stages k_first .. k_first + n_k - 1 (one CTA per speed row and stage).
+cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k_first, int n_k,
+                              StageScratch sc, cudaStream_t s);
 cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
                            const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s);
 cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float *padded, cudaStream_t s);

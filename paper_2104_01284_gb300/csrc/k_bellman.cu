@@ -19,14 +19,26 @@
 //
 // Two variants compute bit-identical results:
 //   * bellman_direct: one thread per state, every control evaluated with its
-//     own G reads (reference layout of the paper's second kernel, Sec. IV);
-//   * bellman_tiled: one thread per (RJ SoC rows, one time node); per class a
-//     register window of RJ + 4 blended values G, the controls of the class
-//     grouped by SoC shift d in {-2, -1, 0, 1} so the window offsets are
-//     compile-time constants; the class tables of the speed row staged in
-//     shared memory.  It tracks only the minimum value per class; the argmin
-//     is recovered after the sweep by re-evaluating the winning class, whose
-//     values are reproduced bit for bit.
+//     own G reads (the layout of the paper's second kernel, Sec. IV);
+//   * bellman_tiled: one CTA per (speed row, 128 lanes); each lane owns one
+//     (SoC group of RJ rows, time node) pair, the pairs of a row laid out back
+//     to back so no lane idles on a ragged time axis.  The row's class and
+//     control tables are staged in shared memory.  Per class a lane holds a
+//     register window of RJ + 4 blended values G; the controls of the class
+//     are grouped by SoC shift d in {-2, -1, 0, 1} so window offsets are
+//     compile-time constants; two rows go through one packed FP32 FMA
+//     (__ffma2_rn) and two controls through one three-input min.  Only the
+//     per-class minimum is kept in the sweep; afterwards each warp buckets
+//     its states by winning class in shared memory and re-evaluates each
+//     state's winning class (bit for bit the same arithmetic) to recover the
+//     lowest control index that reaches the minimum.
+//
+// Argmin order: (value, torque class, control index).  Among controls with
+// exactly equal FP32 values the first class in class order (total torque
+// ascending, brake flag fastest) wins, then the lowest control index inside
+// it.  Exact FP32 ties are rounding coincidences of near-equal costs (the
+// FP64 recursion has none on the seeded instances); resolving them toward the
+// lowest global control index would re-evaluate every tied class.
 #include <cfloat>
 #include <climits>
 
@@ -37,11 +49,12 @@ namespace ecodp {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int TW = 4;  // warps per CTA of the tiled kernel
+constexpr int TLANES = TW * 32;
 
-// Per-thread interpolation context of one class.
+// Per-lane interpolation context of one class.
 struct TCtx {
-    const float *r0, *r1;  // speed rows iv, iv+1 of J_{k+1}, at padded SoC row 0
-    int ta, tb;            // time columns (clamped to the padding column n_t)
+    const float *p0, *p1;  // speed rows iv, iv+1 of J_{k+1} at padded SoC row 0, lower time column
     float wv0, wv1, wt0, wt1;
     bool red;              // arrival during red: every value of the class is infeasible
 };
@@ -66,15 +79,16 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *__res
         snap_split(__fdiv_rn(__fadd_rn(wait, C.dt), P.h_t), st, ft);
         t0 = l + st;
     }
-    x.ta = min(t0, P.n_t);
-    x.tb = min(t0 + 1, P.n_t);
+    // a lower corner past the grid reads the padding column n_t; the upper
+    // corner is the next column, still inside the row (ld_t >= n_t + 2)
+    const int ta = min(t0, P.n_t);
     x.wt1 = ft;
     x.wt0 = __fsub_rn(1.f, ft);
     x.wv1 = C.fv;
     x.wv0 = __fsub_rn(1.f, C.fv);
     const size_t vrow = (size_t)P.xi_rows * P.ld_t;
-    x.r0 = Vn + (size_t)C.iv * vrow;
-    x.r1 = x.r0 + vrow;
+    x.p0 = Vn + (size_t)C.iv * vrow + ta;
+    x.p1 = x.p0 + vrow;
     x.red = false;
     if (si.next_light >= 0 && C.v1 > 0.f) {
         float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
@@ -83,25 +97,36 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *__res
     return x;
 }
 
+__device__ __forceinline__ int row_offset(const DevParams &P, int j)
+{
+    return (min(max(j, -1), P.n_xi) + 1) * P.ld_t;
+}
+
 // Blended value G at SoC row j (any integer; rows outside the grid read padding).
 __device__ __forceinline__ float g_at(const DevParams &P, const TCtx &x, int j)
 {
-    if (x.red)
-        return V_BIG;
-    int jp = min(max(j, -1), P.n_xi) + 1;
-    size_t o = (size_t)jp * P.ld_t;
-    return g_blend(x.r0 + o, x.r1 + o, x.ta, x.tb, x.wv0, x.wv1, x.wt0, x.wt1);
+    const int o = row_offset(P, j);
+    const float g = g_blend2(x.p0 + o, x.p1 + o, x.wv0, x.wv1, x.wt0, x.wt1);
+    return x.red ? V_BIG : g;
 }
 
-__device__ __forceinline__ float split_value(const float4 &S, float g0, float g1)
+// c + w0 g0 + w1 g1, in this order (the packed path rounds identically).
+__device__ __forceinline__ float split_value(const SplitRec &S, float g0, float g1)
 {
-    return __fmaf_rn(S.z, g1, __fmaf_rn(S.y, g0, S.x));
+    return __fmaf_rn(S.w1, g1, __fmaf_rn(S.w0, g0, S.c));
 }
 
-__device__ __forceinline__ int split_u(const float4 &S) { return (int)(__float_as_uint(S.w) & 0xffffu); }
-__device__ __forceinline__ int split_d(const float4 &S) { return (int)(short)(__float_as_uint(S.w) >> 16); }
+__device__ __forceinline__ int split_u(const SplitRec &S) { return (int)(S.bits & 0xffffu); }
+__device__ __forceinline__ int split_d(const SplitRec &S) { return (int)(short)(S.bits >> 16); }
 
-__device__ __forceinline__ StageInfo stage_info(const DevParams &P, const StageTables &tb, int k, float v)
+__device__ __forceinline__ float min3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ StageInfo stage_info(const StageTables &tb, int k, float v)
 {
     StageInfo si;
     int lk = tb.light_of_node[k];
@@ -145,25 +170,28 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     const int j = s / P.n_t, l = s % P.n_t;
     const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
     const float tl = node_val(P.t_lo, P.t_span, l, P.n_t);
-    const StageInfo si = stage_info(P, tb, k, v);
+    const StageInfo si = stage_info(tb, k, v);
     const float wait = wait_time(tb, k, tl, si.wait_row);
-    const int n_ent = sc.row_cnt[2 * i];
-    const ClassRec *cls = sc.cls + (size_t)i * P.n_cls;
-    const ClassEntry *ent = sc.ent + (size_t)i * P.n_cls;
-    const float4 *spl = sc.spl + (size_t)i * P.n_u;
+    const size_t row = (size_t)k * P.n_v + i;
+    const int n_ent = sc.row_cnt[2 * row];
+    const ClassRec *cls = sc.cls + row * P.n_cls;
+    const ClassEntry *ent = sc.ent + row * P.n_cls;
+    const SplitRec *spl = sc.spl + row * P.n_u;
 
+    // minimum in the order (value, class, control index)
     float best = __int_as_float(0x7f800000);
-    int bu = INT_MAX;
+    int bu = INT_MAX, be = -1;
     for (int e = 0; e < n_ent; ++e) {
         const ClassEntry E = ent[e];
         const TCtx x = class_ctx(P, Vn, cls[E.cls], l, tl, wait, si);
         for (int q = E.off; q < E.off + E.n_total; ++q) {
-            const float4 S = spl[q];
+            const SplitRec S = spl[q];
             const int d = split_d(S), u = split_u(S);
             const float F = split_value(S, g_at(P, x, j + d), g_at(P, x, j + d + 1));
-            if (F < best || (F == best && u < bu)) {
+            if (F < best || (F == best && e == be && u < bu)) {
                 best = F;
                 bu = u;
+                be = e;
             }
         }
     }
@@ -181,212 +209,304 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
 // ---------------------------------------------------------------------------
 // tiled variant
 
-struct RowSmem {
-    const ClassRec *cls;
-    const ClassEntry *ent;
-    const float4 *spl;
-};
-
-// Minimum over the controls of class E for the thread's RJ rows.
-__device__ __forceinline__ void class_min(const DevParams &P, const TCtx &x, const ClassEntry &E,
-                                          const float4 *__restrict__ spl, int jb, float (&cm)[RJ])
+// Minimum over the controls of one SoC-shift bucket: row r uses window values
+// G[r + D + 2] and G[r + D + 3].  EV holds the even-aligned pairs
+// {G[2p], G[2p+1]}, OD the odd-aligned pairs {G[2p+1], G[2p+2]}.
+template <int D>
+__device__ __forceinline__ void bucket_min(const SplitRec *__restrict__ spl, int q, int n,
+                                           const float2 (&EV)[RJ / 2 + 2], const float2 (&OD)[RJ / 2 + 1],
+                                           float (&cm)[RJ])
 {
-    float G[RJ + 4];
+    const int end = q + n;
+    for (; q + 1 < end; q += 2) {
+        const SplitRec s1 = spl[q], s2 = spl[q + 1];
+        const float2 c1 = make_float2(s1.c, s1.c), w01 = make_float2(s1.w0, s1.w0), w11 = make_float2(s1.w1, s1.w1);
+        const float2 c2 = make_float2(s2.c, s2.c), w02 = make_float2(s2.w0, s2.w0), w12 = make_float2(s2.w1, s2.w1);
 #pragma unroll
-    for (int w = 0; w < RJ + 4; ++w)
-        G[w] = g_at(P, x, jb - 2 + w);
-#pragma unroll
-    for (int r = 0; r < RJ; ++r)
-        cm[r] = __int_as_float(0x7f800000);
-    int q = E.off;
-#define ECODP_BUCKET(NB, D)                                                                   \
-    for (int n = 0; n < (NB); ++n, ++q) {                                                    \
-        const float4 S = spl[q];                                                             \
-        _Pragma("unroll") for (int r = 0; r < RJ; ++r) cm[r] =                                \
-            fminf(cm[r], split_value(S, G[r + (D) + 2], G[r + (D) + 3]));                      \
+        for (int p = 0; p < RJ / 2; ++p) {
+            const float2 LO = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 HI = ((D & 1) == 0) ? OD[p + (D + 2) / 2] : EV[p + (D + 3) / 2];
+            const float2 F1 = __ffma2_rn(w11, HI, __ffma2_rn(w01, LO, c1));
+            const float2 F2 = __ffma2_rn(w12, HI, __ffma2_rn(w02, LO, c2));
+            cm[2 * p] = min3(cm[2 * p], F1.x, F2.x);
+            cm[2 * p + 1] = min3(cm[2 * p + 1], F1.y, F2.y);
+        }
     }
-    ECODP_BUCKET(E.nb[0], -2)
-    ECODP_BUCKET(E.nb[1], -1)
-    ECODP_BUCKET(E.nb[2], 0)
-    ECODP_BUCKET(E.nb[3], 1)
-#undef ECODP_BUCKET
-    for (int n = 0; n < E.n_other; ++n, ++q) {
-        const float4 S = spl[q];
-        const int d = split_d(S);
+    if (q < end) {
+        const SplitRec s1 = spl[q];
+        const float2 c1 = make_float2(s1.c, s1.c), w01 = make_float2(s1.w0, s1.w0), w11 = make_float2(s1.w1, s1.w1);
 #pragma unroll
-        for (int r = 0; r < RJ; ++r)
-            cm[r] = fminf(cm[r], split_value(S, g_at(P, x, jb + r + d), g_at(P, x, jb + r + d + 1)));
-    }
-}
-
-// Lowest control index of class E whose value equals best[r], for rows in mask.
-__device__ __forceinline__ void class_find(const DevParams &P, const TCtx &x, const ClassEntry &E,
-                                           const float4 *__restrict__ spl, int jb, unsigned rows,
-                                           const float (&best)[RJ], int (&ub)[RJ])
-{
-    for (int q = E.off; q < E.off + E.n_total; ++q) {
-        const float4 S = spl[q];
-        const int d = split_d(S), u = split_u(S);
-#pragma unroll
-        for (int r = 0; r < RJ; ++r) {
-            if ((rows >> r) & 1u) {
-                const float F = split_value(S, g_at(P, x, jb + r + d), g_at(P, x, jb + r + d + 1));
-                if (F == best[r] && u < ub[r])
-                    ub[r] = u;
-            }
+        for (int p = 0; p < RJ / 2; ++p) {
+            const float2 LO = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 HI = ((D & 1) == 0) ? OD[p + (D + 2) / 2] : EV[p + (D + 3) / 2];
+            const float2 F1 = __ffma2_rn(w11, HI, __ffma2_rn(w01, LO, c1));
+            cm[2 * p] = fminf(cm[2 * p], F1.x);
+            cm[2 * p + 1] = fminf(cm[2 * p + 1], F1.y);
         }
     }
 }
 
-template <bool SMEM_SPLITS>
-__global__ void __launch_bounds__(256) bellman_tiled(const DevParams *__restrict__ dP, StageTables tb, int k,
-                                                     StageScratch sc, const float *__restrict__ Vn,
-                                                     float *__restrict__ Vk, int16_t *__restrict__ pik)
+// Lowest control index of class E whose value at SoC row j equals bv (INT_MAX
+// if none), re-evaluated with exactly the arithmetic of the sweep.
+__device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x, const ClassEntry &E,
+                                              const SplitRec *__restrict__ spl, int j, float bv)
+{
+    float g5[5];  // SoC rows j - 2 .. j + 2
+#pragma unroll
+    for (int w = 0; w < 5; ++w)
+        g5[w] = g_at(P, x, j - 2 + w);
+    int ub = INT_MAX;
+    int q = E.off;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {  // bucket b holds the shift d = b - 2
+        for (int n = 0; n < E.nb[b]; ++n, ++q) {
+            const SplitRec S = spl[q];
+            const int u = split_u(S);
+            if (split_value(S, g5[b], g5[b + 1]) == bv && u < ub)
+                ub = u;
+        }
+    }
+    for (int n = 0; n < E.n_other; ++n, ++q) {
+        const SplitRec S = spl[q];
+        const int d = split_d(S), u = split_u(S);
+        if (split_value(S, g_at(P, x, j + d), g_at(P, x, j + d + 1)) == bv && u < ub)
+            ub = u;
+    }
+    return ub;
+}
+
+constexpr int WSTATES = 32 * RJ;  // states of one warp
+
+// Shared memory of the tiled kernel: the row's tables, then per warp the
+// argmin-recovery buffers: counters [n_cls + 1], entry list [WSTATES], best
+// value per state [WSTATES].
+struct TiledLayout {
+    size_t ent, spl, warp, warp_bytes, total;
+    size_t w_list, w_best;  // offsets inside a warp's block
+};
+
+__host__ __device__ inline TiledLayout tiled_layout(int n_cls, int n_u)
+{
+    TiledLayout L;
+    size_t o = (size_t)n_cls * sizeof(ClassRec);
+    L.ent = o;
+    o += (size_t)n_cls * sizeof(ClassEntry);
+    L.spl = o;
+    o += (size_t)n_u * sizeof(SplitRec);
+    L.warp = o;
+    size_t w = ((size_t)(n_cls + 1) * sizeof(int) + 15) / 16 * 16;
+    L.w_list = w;
+    w += (size_t)WSTATES * sizeof(unsigned);
+    L.w_best = w;
+    w += (size_t)WSTATES * sizeof(float);
+    L.warp_bytes = w;
+    L.total = o + TW * L.warp_bytes;
+    return L;
+}
+
+__global__ void __launch_bounds__(TLANES, 4) bellman_tiled(const DevParams *__restrict__ dP, StageTables tb, int k,
+                                                          StageScratch sc, const float *__restrict__ Vn,
+                                                          float *__restrict__ Vk, int16_t *__restrict__ pik)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevParams P;
-    if (threadIdx.x == 0 && threadIdx.y == 0)
+    const int tid = threadIdx.x;
+    if (tid == 0)
         P = *dP;
     __syncthreads();
 
     const int i = blockIdx.y;
-    const int n_ent = sc.row_cnt[2 * i];
-    const int n_spl = sc.row_cnt[2 * i + 1];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthr = blockDim.x * blockDim.y;
-
-    // stage the row's tables: ClassRec[n_cls], ClassEntry[n_ent], float4[n_spl]
+    const size_t row = (size_t)k * P.n_v + i;
+    const int n_ent = sc.row_cnt[2 * row];
+    const int n_spl = sc.row_cnt[2 * row + 1];
+    const TiledLayout L = tiled_layout(P.n_cls, P.n_u);
     ClassRec *s_cls = reinterpret_cast<ClassRec *>(smem_raw);
-    ClassEntry *s_ent = reinterpret_cast<ClassEntry *>(s_cls + P.n_cls);
-    float4 *s_spl = reinterpret_cast<float4 *>(s_ent + n_ent);
+    ClassEntry *s_ent = reinterpret_cast<ClassEntry *>(smem_raw + L.ent);
+    SplitRec *s_spl = reinterpret_cast<SplitRec *>(smem_raw + L.spl);
     {
-        const int4 *src = reinterpret_cast<const int4 *>(sc.cls + (size_t)i * P.n_cls);
+        const int4 *src = reinterpret_cast<const int4 *>(sc.cls + row * P.n_cls);
         int4 *dst = reinterpret_cast<int4 *>(s_cls);
-        for (int q = tid; q < P.n_cls * 2; q += nthr)
+        for (int q = tid; q < P.n_cls * 2; q += TLANES)
             dst[q] = src[q];
-        const int4 *src2 = reinterpret_cast<const int4 *>(sc.ent + (size_t)i * P.n_cls);
+        const int4 *src2 = reinterpret_cast<const int4 *>(sc.ent + row * P.n_cls);
         int4 *dst2 = reinterpret_cast<int4 *>(s_ent);
-        for (int q = tid; q < n_ent * 2; q += nthr)
+        for (int q = tid; q < n_ent * 2; q += TLANES)
             dst2[q] = src2[q];
-        if (SMEM_SPLITS) {
-            const float4 *src3 = sc.spl + (size_t)i * P.n_u;
-            for (int q = tid; q < n_spl; q += nthr)
-                s_spl[q] = src3[q];
-        }
+        const int4 *src3 = reinterpret_cast<const int4 *>(sc.spl + row * P.n_u);
+        int4 *dst3 = reinterpret_cast<int4 *>(s_spl);
+        for (int q = tid; q < n_spl; q += TLANES)
+            dst3[q] = src3[q];
     }
+    const int warp = tid >> 5, lane = tid & 31;
+    unsigned char *wbase = smem_raw + L.warp + warp * L.warp_bytes;
+    int *w_cnt = reinterpret_cast<int *>(wbase);
+    unsigned *w_list = reinterpret_cast<unsigned *>(wbase + L.w_list);
+    float *w_best = reinterpret_cast<float *>(wbase + L.w_best);
     __syncthreads();
-    const float4 *spl = SMEM_SPLITS ? s_spl : sc.spl + (size_t)i * P.n_u;
 
-    const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
-    const StageInfo si = stage_info(P, tb, k, v);
-    const int jb = (blockIdx.x * blockDim.y + threadIdx.y) * RJ;
+    const int n_jg = (P.n_xi + RJ - 1) / RJ;
+    const int n_flat = n_jg * P.n_t;
+    const int chunk0 = blockIdx.x * TLANES + warp * 32;  // first flat index of this warp
+    const int f_raw = chunk0 + lane;
+    const bool f_ok = f_raw < n_flat;
+    const int f = f_ok ? f_raw : n_flat - 1;
+    const int jg = f / P.n_t;
+    const int l = f - jg * P.n_t;
+    const int jb = jg * RJ;
     const float one_m_gamma = __fsub_rn(1.f, P.gamma);
+    const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
+    const StageInfo si = stage_info(tb, k, v);
+    const float tl = node_val(P.t_lo, P.t_span, l, P.n_t);
+    const float wait = wait_time(tb, k, tl, si.wait_row);
 
-    for (int l0 = 0; l0 < P.n_t; l0 += blockDim.x) {
-        const int l_raw = l0 + threadIdx.x;
-        const bool l_ok = l_raw < P.n_t;
-        const int l = l_ok ? l_raw : P.n_t - 1;
-        const float tl = node_val(P.t_lo, P.t_span, l, P.n_t);
-        const float wait = wait_time(tb, k, tl, si.wait_row);
+    int roff[RJ + 4];
+#pragma unroll
+    for (int w = 0; w < RJ + 4; ++w)
+        roff[w] = row_offset(P, jb - 2 + w);
 
-        float best[RJ];
-        int bcls[RJ];
-        unsigned tie = 0;
+    // per row: the running minimum and the first class (in class order)
+    // reaching it; `tie` marks rows whose minimum a later class matches
+    // exactly (counted only: the order (value, class, control) decides)
+    float best[RJ];
+    int bcls[RJ];
+    unsigned tie = 0;
+#pragma unroll
+    for (int r = 0; r < RJ; ++r) {
+        best[r] = __int_as_float(0x7f800000);
+        bcls[r] = 0;
+    }
+    for (int e = 0; e < n_ent; ++e) {
+        const ClassEntry E = s_ent[e];
+        const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
+        float G[RJ + 4];
+#pragma unroll
+        for (int w = 0; w < RJ + 4; ++w) {
+            const float g = g_blend2(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
+            G[w] = x.red ? V_BIG : g;
+        }
+        float2 EV[RJ / 2 + 2], OD[RJ / 2 + 1];
+#pragma unroll
+        for (int p = 0; p < RJ / 2 + 2; ++p)
+            EV[p] = make_float2(G[2 * p], G[2 * p + 1]);
+#pragma unroll
+        for (int p = 0; p < RJ / 2 + 1; ++p)
+            OD[p] = make_float2(G[2 * p + 1], G[2 * p + 2]);
+        float cm[RJ];
+#pragma unroll
+        for (int r = 0; r < RJ; ++r)
+            cm[r] = __int_as_float(0x7f800000);
+        int q = E.off;
+        bucket_min<-2>(s_spl, q, E.nb[0], EV, OD, cm);
+        q += E.nb[0];
+        bucket_min<-1>(s_spl, q, E.nb[1], EV, OD, cm);
+        q += E.nb[1];
+        bucket_min<0>(s_spl, q, E.nb[2], EV, OD, cm);
+        q += E.nb[2];
+        bucket_min<1>(s_spl, q, E.nb[3], EV, OD, cm);
+        q += E.nb[3];
+        for (int n = 0; n < E.n_other; ++n, ++q) {
+            const SplitRec S = s_spl[q];
+            const int d = split_d(S);
+#pragma unroll
+            for (int r = 0; r < RJ; ++r)
+                cm[r] = fminf(cm[r], split_value(S, g_at(P, x, jb + r + d), g_at(P, x, jb + r + d + 1)));
+        }
 #pragma unroll
         for (int r = 0; r < RJ; ++r) {
-            best[r] = __int_as_float(0x7f800000);
-            bcls[r] = -1;
-        }
-        for (int e = 0; e < n_ent; ++e) {
-            const ClassEntry E = s_ent[e];
-            const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
-            float cm[RJ];
-            class_min(P, x, E, spl, jb, cm);
-#pragma unroll
-            for (int r = 0; r < RJ; ++r) {
-                if (cm[r] < best[r]) {
-                    best[r] = cm[r];
-                    bcls[r] = e;
-                } else if (cm[r] == best[r] && cm[r] < V_FEAS_MAX) {
-                    tie |= 1u << r;
-                }
+            if (cm[r] < best[r]) {
+                best[r] = cm[r];
+                bcls[r] = e;
+                tie &= ~(1u << r);
+            } else if (cm[r] == best[r]) {
+                tie |= 1u << r;
             }
         }
+    }
 
-        // argmin recovery: lowest control index reproducing the minimum
-        unsigned todo = 0;
+    // values now; argmin recovery below
+    unsigned todo = 0;
 #pragma unroll
-        for (int r = 0; r < RJ; ++r)
-            if (l_ok && jb + r < P.n_xi && best[r] < V_FEAS_MAX)
-                todo |= 1u << r;
-        tie &= todo;
-        int ub[RJ];
-#pragma unroll
-        for (int r = 0; r < RJ; ++r)
-            ub[r] = INT_MAX;
-        if (__any_sync(FULL, tie != 0u)) {
-            for (int e = 0; e < n_ent; ++e) {
-                unsigned rows = 0;
-#pragma unroll
-                for (int r = 0; r < RJ; ++r)
-                    if (((todo >> r) & 1u) && (((tie >> r) & 1u) || bcls[r] == e))
-                        rows |= 1u << r;
-                if (__any_sync(FULL, rows != 0u)) {
-                    const ClassEntry E = s_ent[e];
-                    const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
-                    class_find(P, x, E, spl, jb, rows, best, ub);
-                }
-            }
-        } else {
-            unsigned left = todo;
-            while (__any_sync(FULL, left != 0u)) {
-                int mine = INT_MAX;
-#pragma unroll
-                for (int r = 0; r < RJ; ++r)
-                    if ((left >> r) & 1u)
-                        mine = min(mine, bcls[r]);
-                const int e = __reduce_min_sync(FULL, mine);
-                unsigned rows = 0;
-#pragma unroll
-                for (int r = 0; r < RJ; ++r)
-                    if (((left >> r) & 1u) && bcls[r] == e)
-                        rows |= 1u << r;
-                const ClassEntry E = s_ent[e];
-                const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
-                class_find(P, x, E, spl, jb, rows, best, ub);
-                left &= ~rows;
-            }
+    for (int r = 0; r < RJ; ++r) {
+        const int j = jb + r;
+        const bool valid = f_ok && j < P.n_xi;
+        const bool feas = valid && best[r] < V_FEAS_MAX;
+        if (feas)
+            todo |= 1u << r;
+        if (valid) {
+            Vk[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] =
+                feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
+            if (!feas)
+                pik[((size_t)i * P.n_xi + j) * P.n_t + l] = -1;
         }
+    }
+    tie &= todo;
+    if (sc.stats) {
+        const unsigned n_tie = __reduce_add_sync(FULL, (unsigned)__popc(tie));
+        const unsigned n_find = __reduce_add_sync(FULL, (unsigned)__popc(todo));
+        if (lane == 0) {
+            atomicAdd(sc.stats + 2, (unsigned long long)n_tie);
+            atomicAdd(sc.stats + 3, (unsigned long long)n_find);
+        }
+    }
 
-        if (l_ok) {
+    // bucket the feasible states by their first winning class and recover the
+    // lowest winning control of that class, warp-wide class by class
+    for (int q = lane; q < n_ent; q += 32)
+        w_cnt[q] = 0;
+    __syncwarp();
 #pragma unroll
-            for (int r = 0; r < RJ; ++r) {
-                const int j = jb + r;
-                if (j >= P.n_xi)
-                    continue;
-                const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
-                const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + l;
-                if ((todo >> r) & 1u) {
-                    Vk[o] = __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait));
-                    pik[op] = (int16_t)ub[r];
-                } else {
-                    Vk[o] = V_BIG;
-                    pik[op] = -1;
-                }
-            }
+    for (int r = 0; r < RJ; ++r) {
+        if ((todo >> r) & 1u) {
+            atomicAdd(&w_cnt[bcls[r]], 1);
+            w_best[lane * RJ + r] = best[r];
         }
+    }
+    __syncwarp();
+    int total = 0;  // exclusive scan of the counters, in place
+    for (int b0 = 0; b0 < n_ent; b0 += 32) {
+        const int q = b0 + lane;
+        const int x = q < n_ent ? w_cnt[q] : 0;
+        int incl = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d)
+                incl += y;
+        }
+        if (q < n_ent)
+            w_cnt[q] = total + incl - x;
+        total += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < RJ; ++r) {
+        if ((todo >> r) & 1u) {
+            const int key = bcls[r];
+            const int pos = atomicAdd(&w_cnt[key], 1);
+            w_list[pos] = ((unsigned)key << 16) | (unsigned)(lane * RJ + r);
+        }
+    }
+    __syncwarp();
+    for (int q = lane; q < total; q += 32) {
+        const unsigned en = w_list[q];
+        const int e = (int)(en >> 16);
+        const int s = (int)(en & 0xffffu);
+        const int ln = s / RJ, r = s - ln * RJ;
+        const int fq = chunk0 + ln;
+        const int jgq = fq / P.n_t;
+        const int lq = fq - jgq * P.n_t;
+        const float tlq = node_val(P.t_lo, P.t_span, lq, P.n_t);
+        const float wq = wait_time(tb, k, tlq, si.wait_row);
+        const ClassEntry E = s_ent[e];
+        const TCtx x = class_ctx(P, Vn, s_cls[E.cls], lq, tlq, wq, si);
+        const int j = jgq * RJ + r;
+        pik[((size_t)i * P.n_xi + j) * P.n_t + lq] = (int16_t)class_lowest_u(P, x, E, s_spl, j, w_best[s]);
     }
 }
 
 }  // namespace
 
-size_t bellman_smem_bytes(const DevParams &hP, bool smem_splits)
-{
-    size_t b = (size_t)hP.n_cls * (sizeof(ClassRec) + sizeof(ClassEntry));
-    if (smem_splits)
-        b += (size_t)hP.n_u * sizeof(float4);
-    return b;
-}
+size_t bellman_smem_bytes(const DevParams &hP) { return tiled_layout(hP.n_cls, hP.n_u).total; }
 
 cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
                            const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s)
@@ -396,25 +516,13 @@ cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables
         bellman_direct<<<grid, 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
         return cudaGetLastError();
     }
-    const int tx = min(256, round_up(hP.n_t, 32));
-    const int ty = tx <= 128 ? 2 : 1;
-    const int n_groups = (hP.n_xi + RJ - 1) / RJ;
-    dim3 block(tx, ty);
-    dim3 grid((n_groups + ty - 1) / ty, hP.n_v);
-    const bool smem_splits = bellman_smem_bytes(hP, true) <= 160 * 1024;
-    const size_t smem = bellman_smem_bytes(hP, smem_splits);
-    cudaError_t err;
-    if (smem_splits) {
-        err = cudaFuncSetAttribute(bellman_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess)
-            return err;
-        bellman_tiled<true><<<grid, block, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
-    } else {
-        err = cudaFuncSetAttribute(bellman_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess)
-            return err;
-        bellman_tiled<false><<<grid, block, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
-    }
+    const size_t smem = bellman_smem_bytes(hP);
+    cudaError_t err = cudaFuncSetAttribute(bellman_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return err;
+    const int n_jg = (hP.n_xi + RJ - 1) / RJ;
+    const int chunks = (n_jg * hP.n_t + TLANES - 1) / TLANES;
+    bellman_tiled<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
     return cudaGetLastError();
 }
 

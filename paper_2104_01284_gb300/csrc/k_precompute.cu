@@ -3,14 +3,17 @@
 //
 // The paper's first kernel evaluates, per (v, T_eng, T_bsg), the speed change,
 // the step time, the battery power and the stage cost.  Here one CTA handles
-// one speed row v_i of stage k and writes
+// one speed row v_i of one stage k (all stages of a sweep in one launch) and
+// writes into the stage's table slot
 //   * one ClassRec per torque class (speed update Eq. 5a, step time Eq. 2,
 //     acceleration limits Eq. 7d, stop-at-line rule, speed-grid band Eq. 7a)
 //     with the speed-axis and time-axis interpolation already resolved;
 //   * the compact list of feasible classes (ClassEntry) in class order;
-//   * per feasible control one float4 {cost, w0, w1, u | d << 16}: the stage
-//     cost of Eq. (1)/(6), and the SoC-axis shift d and weights (1-f, f) of
-//     xi' = xi - dt I / C_nom (Eq. 5b), grouped inside each class by d.
+//   * per feasible control one SplitRec: the stage cost of Eq. (1)/(6), and
+//     the SoC-axis shift d and weights (1-f, f) of xi' = xi - dt I / C_nom
+//     (Eq. 5b), grouped inside each class by d.
+// The per-control arithmetic runs one thread per control; the grouping then
+// only reads those results back from shared memory.
 #include "ecodp_internal.cuh"
 
 namespace ecodp {
@@ -61,7 +64,7 @@ __global__ void dense_from_pad_kernel(const DevParams P, const float *__restrict
     }
 }
 
-// Members (i_e, i_m) of class c in increasing i_e order.
+// Members (i_e, i_m) of class c in increasing i_e order (increasing u).
 struct Members {
     int ie_lo, ie_hi, s;  // class_sum: i_m = s - i_e; otherwise one member
     int im_single;
@@ -86,8 +89,13 @@ __device__ __forceinline__ Members class_members(const DevParams &P, int c)
 
 __device__ __forceinline__ int member_im(const Members &m, int ie) { return m.im_single >= 0 ? m.im_single : m.s - ie; }
 
+__device__ __forceinline__ int class_of(const DevParams &P, int ie, int im, int b)
+{
+    return (P.class_sum ? (ie + im) : (ie * P.n_tm + im)) * P.n_b + b;
+}
+
 // Block-wide exclusive scan of one int per thread; returns the prefix and
-// writes the block total.  buf holds blockDim.x + 1 ints.
+// writes the block total.  buf holds blockDim.x ints.
 __device__ int block_exclusive_scan(int x, int *buf, int &total)
 {
     int tid = threadIdx.x;
@@ -105,16 +113,25 @@ __device__ int block_exclusive_scan(int x, int *buf, int &total)
     return incl - x;
 }
 
-__global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb, int k,
-                                                         StageScratch sc)
+// shared per-control result
+struct CtrlRec {
+    float cost, f;
+    int d, ok;
+};
+
+__global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
+                                                         int k_first, StageScratch sc)
 {
+    extern __shared__ __align__(16) unsigned char pre_smem[];
+    CtrlRec *s_ctrl = reinterpret_cast<CtrlRec *>(pre_smem);
     __shared__ DevParams P;
-    __shared__ int scan_buf[256 + 1];
+    __shared__ int scan_buf[256];
     if (threadIdx.x == 0)
         P = *dP;
     __syncthreads();
 
     const int i = blockIdx.x;
+    const int k = k_first + blockIdx.y;
     const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
     const float p = tb.grade[k];
     const float sq = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(p, p)));
@@ -124,62 +141,84 @@ __global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__rest
     const float w = __fmul_rn(v, P.ratio);
     const float one_m_gamma = __fsub_rn(1.f, P.gamma);
 
-    ClassRec *cls_row = sc.cls + (size_t)i * P.n_cls;
-    ClassEntry *ent_row = sc.ent + (size_t)i * P.n_cls;
-    float4 *spl_row = sc.spl + (size_t)i * P.n_u;
+    const size_t row = (size_t)k * P.n_v + i;
+    ClassRec *cls_row = sc.cls + row * P.n_cls;
+    ClassEntry *ent_row = sc.ent + row * P.n_cls;
+    SplitRec *spl_row = sc.spl + row * P.n_u;
 
+    // 1. classes: speed update, step time, speed-axis band and interpolation
+    for (int c = threadIdx.x; c < P.n_cls; c += blockDim.x) {
+        const int b = c % P.n_b;
+        const Members mem = class_members(P, c);
+        const int ie0 = mem.ie_lo, im0 = member_im(mem, ie0);
+        const float T =
+            __fadd_rn(node_val(P.te_lo, P.te_span, ie0, P.n_te), node_val(P.tm_lo, P.tm_span, im0, P.n_tm));
+        ClassRec rec = {};
+        float v1 = 0.f, dt = 0.f;
+        bool ok = speed_step(P, v, F_road, T, b, next_light, v1, dt);
+        if (ok) {
+            float qv = __fdiv_rn(__fsub_rn(v1, P.v_lo), P.h_v);
+            float top = (float)(P.n_v - 1);
+            if (qv < -SNAP || qv > top + SNAP)
+                ok = false;
+            qv = fminf(fmaxf(qv, 0.f), top);
+            int iv;
+            float fv;
+            snap_split(qv, iv, fv);
+            if (iv >= P.n_v - 1) {
+                iv = P.n_v - 2;
+                fv = 1.f;
+            }
+            int st;
+            float ft;
+            snap_split(__fdiv_rn(dt, P.h_t), st, ft);
+            rec.iv = iv;
+            rec.fv = fv;
+            rec.v1 = v1;
+            rec.dt = dt;
+            rec.st = st;
+            rec.ft = ft;
+        }
+        rec.ok = ok;
+        cls_row[c] = rec;
+    }
+    __syncthreads();
+
+    // 2. controls: battery (Eq. 5b), SoC shift, stage cost (Eq. 1/6)
+    for (int u = threadIdx.x; u < P.n_u; u += blockDim.x) {
+        int ie, im, b;
+        decode_u(P, u, ie, im, b);
+        const ClassRec C = cls_row[class_of(P, ie, im, b)];
+        CtrlRec r = {0.f, 0.f, 0, 0};
+        float I;
+        const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
+        if (C.ok && battery_current(P, w, Tm, I)) {
+            const float dxi = __fdiv_rn(__fmul_rn(C.dt, I), P.cap);
+            snap_split(__fdiv_rn(-dxi, P.h_xi), r.d, r.f);
+            const float mf = fuel_rate(P, w, node_val(P.te_lo, P.te_span, ie, P.n_te));
+            r.cost = __fmul_rn(__fadd_rn(__fmul_rn(P.gamma, mf), one_m_gamma), C.dt);
+            r.ok = 1;
+        }
+        s_ctrl[u] = r;
+    }
+    __syncthreads();
+
+    // 3. compact the feasible classes and group each class's controls by d
     int ent_carry = 0, spl_carry = 0;
     for (int c0 = 0; c0 < P.n_cls; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
-        ClassRec rec = {};
-        int nspl = 0;
         Members mem = {};
+        int nspl = 0;
         if (c < P.n_cls) {
-            const int b = c % P.n_b;
             mem = class_members(P, c);
-            const int ie0 = mem.ie_lo, im0 = member_im(mem, ie0);
-            const float T = __fadd_rn(node_val(P.te_lo, P.te_span, ie0, P.n_te),
-                                      node_val(P.tm_lo, P.tm_span, im0, P.n_tm));
-            float v1 = 0.f, dt = 0.f;
-            bool ok = speed_step(P, v, F_road, T, b, next_light, v1, dt);
-            if (ok) {
-                // speed-axis band (Eq. 7a) and interpolation cell
-                float qv = __fdiv_rn(__fsub_rn(v1, P.v_lo), P.h_v);
-                float top = (float)(P.n_v - 1);
-                if (qv < -SNAP || qv > top + SNAP)
-                    ok = false;
-                qv = fminf(fmaxf(qv, 0.f), top);
-                int iv;
-                float fv;
-                snap_split(qv, iv, fv);
-                if (iv >= P.n_v - 1) {
-                    iv = P.n_v - 2;
-                    fv = 1.f;
-                }
-                int st;
-                float ft;
-                snap_split(__fdiv_rn(dt, P.h_t), st, ft);
-                rec.iv = iv;
-                rec.fv = fv;
-                rec.v1 = v1;
-                rec.dt = dt;
-                rec.st = st;
-                rec.ft = ft;
-            }
-            rec.ok = ok;
-            if (ok) {
-                for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
-                    float I;
-                    float Tm = node_val(P.tm_lo, P.tm_span, member_im(mem, ie), P.n_tm);
-                    nspl += battery_current(P, w, Tm, I) ? 1 : 0;
-                }
-            }
-            cls_row[c] = rec;
+            const int b = c % P.n_b;
+            for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie)
+                nspl += s_ctrl[(ie * P.n_tm + member_im(mem, ie)) * P.n_b + b].ok;
         }
-        const int feas = (c < P.n_cls && rec.ok && nspl > 0) ? 1 : 0;
+        const int feas = nspl > 0 ? 1 : 0;
         int ent_tot, spl_tot;
         const int ent_idx = block_exclusive_scan(feas, scan_buf, ent_tot) + ent_carry;
-        const int spl_off = block_exclusive_scan(feas ? nspl : 0, scan_buf, spl_tot) + spl_carry;
+        const int spl_off = block_exclusive_scan(nspl, scan_buf, spl_tot) + spl_carry;
         if (feas) {
             const int b = c % P.n_b;
             ClassEntry E;
@@ -187,28 +226,21 @@ __global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__rest
             E.off = spl_off;
             E.n_total = nspl;
             int pos = spl_off;
-            // buckets d = -2, -1, 0, +1, then every other shift
             for (int bucket = 0; bucket < 5; ++bucket) {
                 int cnt = 0;
                 for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
                     const int im = member_im(mem, ie);
-                    const float Te = node_val(P.te_lo, P.te_span, ie, P.n_te);
-                    const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
-                    float I;
-                    if (!battery_current(P, w, Tm, I))
-                        continue;
-                    const float dxi = __fdiv_rn(__fmul_rn(rec.dt, I), P.cap);
-                    int d;
-                    float f;
-                    snap_split(__fdiv_rn(-dxi, P.h_xi), d, f);
-                    const bool in4 = d >= -2 && d <= 1;
-                    if (bucket < 4 ? (d != bucket - 2) : in4)
-                        continue;
-                    const float mf = fuel_rate(P, w, Te);
-                    const float cost = __fmul_rn(__fadd_rn(__fmul_rn(P.gamma, mf), one_m_gamma), rec.dt);
                     const int u = (ie * P.n_tm + im) * P.n_b + b;
-                    const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(d & 0xffff) << 16);
-                    spl_row[pos++] = make_float4(cost, __fsub_rn(1.f, f), f, __uint_as_float(bits));
+                    const CtrlRec r = s_ctrl[u];
+                    if (!r.ok)
+                        continue;
+                    const bool in4 = r.d >= -2 && r.d <= 1;
+                    if (bucket < 4 ? (r.d != bucket - 2) : in4)
+                        continue;
+                    const float w0 = __fsub_rn(1.f, r.f);
+                    const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(r.d & 0xffff) << 16);
+                    spl_row[pos] = SplitRec{r.cost, w0, r.f, bits};
+                    ++pos;
                     ++cnt;
                 }
                 if (bucket < 4)
@@ -222,8 +254,8 @@ __global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__rest
         spl_carry += spl_tot;
     }
     if (threadIdx.x == 0) {
-        sc.row_cnt[2 * i] = ent_carry;
-        sc.row_cnt[2 * i + 1] = spl_carry;
+        sc.row_cnt[2 * row] = ent_carry;
+        sc.row_cnt[2 * row + 1] = spl_carry;
         if (sc.stats) {
             atomicAdd(sc.stats, (unsigned long long)spl_carry);
             atomicAdd(sc.stats + 1, (unsigned long long)ent_carry);
@@ -252,10 +284,14 @@ cudaError_t launch_terminal(const DevParams *dP, const DevParams &hP, float *VN,
     return cudaGetLastError();
 }
 
-cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
-                              cudaStream_t s)
+cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k_first, int n_k,
+                              StageScratch sc, cudaStream_t s)
 {
-    precompute_kernel<<<hP.n_v, 256, 0, s>>>(dP, tb, k, sc);
+    const size_t smem = (size_t)hP.n_u * sizeof(CtrlRec);
+    cudaError_t err = cudaFuncSetAttribute(precompute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return err;
+    precompute_kernel<<<dim3(hP.n_v, n_k), 256, smem, s>>>(dP, tb, k_first, sc);
     return cudaGetLastError();
 }
 
