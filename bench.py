@@ -36,9 +36,11 @@ UNIT = "evals/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum per Bellman launch from an ncu
-# capture of the current kernel (None until captured for this kernel version).
-BELLMAN_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one Bellman launch (stage 79
+# of this workload) from an ncu capture of the current kernel version; see
+# profiles/bellman_tiled_c1_stage79.md.  Reset to None whenever the kernel
+# changes until it is captured again.
+BELLMAN_TRAFFIC_BYTES = 4.04e6
 
 
 def parse():
