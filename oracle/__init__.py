@@ -92,6 +92,7 @@ def lib():
             L.orc_rollout.argtypes = [P, vp, vp, vp, vp, vp, vp]
             L.orc_sequence_cost.argtypes = [P, vp, vp, vp]
             L.orc_sequence_cost.restype = C.c_double
+            L.orc_adjoint.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -238,7 +239,7 @@ def solve(op: OracleProblem, mode: int = NOMINAL, nthreads: int = 0):
         if k < N:
             pis.append(piall[o:o + n].reshape(op.shapes[k]))
             secs.append(secall[o:o + n].reshape(op.shapes[k]))
-    op._Vall = Vall
+    op._Vall, op._piall, op._secall = Vall, piall, secall
     return Vs, pis, secs
 
 
@@ -257,6 +258,26 @@ def rollout(op: OracleProblem, Vs, x0=None):
     return dict(traj=traj.reshape(N + 1, 3), u=u, dt=st[:, 0], wait=st[:, 1], fuel=st[:, 2],
                 cost=st[:, 3], gap=st[:, 4], fuel_g=tot[0], time_s=tot[1], J=tot[2],
                 status=int(rc), fail_stage=int(tot[3]))
+
+
+THETA = ("mass", "cda", "crr", "r0", "fuel_scale")
+
+
+def adjoint(op: OracleProblem, x0=None):
+    """dJ_0(x0)/dtheta for theta = THETA by the forward lambda sweep, on the
+    nominal solution of the last `solve(op)` call.  Returns (grad[5], diag
+    dict, support flags over the states of stages 0..N-1, status)."""
+    if getattr(op, "_piall", None) is None:
+        raise RuntimeError("call solve(op) first")
+    x0 = np.array(op.p.x0 if x0 is None else x0, np.float64)
+    grad = np.zeros(5)
+    diag = np.zeros(4)
+    support = np.zeros(op._Vall.size, np.uint8)
+    rc = lib().orc_adjoint(op.ref, _ptr(op._Vall), _ptr(op._piall), _ptr(op._secall), _ptr(x0), _ptr(grad),
+                           _ptr(diag), _ptr(support))
+    d = dict(support_size=int(diag[0]), snapped=bool(diag[1]), infeasible_corner=bool(diag[2]),
+             min_gap=float(diag[3]))
+    return grad, d, support, int(rc)
 
 
 def model_step(op: OracleProblem, k, v, soc, t, Te, Tm, b):

@@ -605,6 +605,223 @@ int orc_rollout(const orc_problem *P, const double *Vall, const double *x0, doub
     return ORC_OK;
 }
 
+/* ---- adjoint: dJ_0(x0)/dtheta by the envelope theorem ------------------------
+ * theta = (mass, CdA, Crr, R0, fuel_scale).  With the argmin fixed,
+ *   J_k(s) = c(s, u*) + I_{k+1}[J_{k+1}](f(s, u*)),
+ * where I_{k+1} is the trilinear interpolant on the stage-(k+1) grid, so
+ *   dJ_0(x0) = sum_k sum_s lam_k(s) [dc/dtheta + grad I_{k+1} . df/dtheta],
+ *   lam_0 = interpolation weights of x0, lam_{k+1}(n) = sum_s lam_k(s) w_n(f(s, u*)).
+ * The derivatives of one step follow Eq. (2), (5a), (5b) and (6) by
+ * differentiating through a, v', dt, I and the fuel map. */
+
+typedef struct {
+    double dv1[5], dxi1[5], dt1[5], dcost[5];
+} orc_dstep;
+
+/* One step with derivatives (nominal decisions).  Returns 1 if feasible. */
+static int transition_grad(const orc_problem *P, int k, double v, double xi, double t, double Te, double Tm, int b,
+                           orc_trans *o, orc_dstep *g)
+{
+    if (!transition(P, k, v, xi, t, Te, Tm, b, NULL, o))
+        return 0;
+    memset(g, 0, sizeof *g);
+    const double M = P->mass;
+    double p = P->grade[k];
+    double sq = sqrt(1.0 + p * p);
+    double cos_th = 1.0 / sq;
+    double ratio = P->gear / P->r_wheel;
+    double da[5] = {0, 0, 0, 0, 0}; /* d a / d theta */
+    da[0] = -((Te + Tm) * ratio - 0.5 * P->rho * P->cda * v * v) / (M * M);
+    da[1] = -0.5 * P->rho * v * v / M;
+    da[2] = -P->g * cos_th;
+    double ddt[5] = {0, 0, 0, 0, 0};
+    if (o->v1 > 0.0) { /* v' = sqrt(v^2 + 2 ds a), dt = 2 ds / (v + v') */
+        for (int q = 0; q < 5; ++q) {
+            g->dv1[q] = P->ds * da[q] / o->v1;
+            ddt[q] = -o->dt / (v + o->v1) * g->dv1[q];
+        }
+    } /* stopping at the line: v' = 0 and dt = 2 ds / v do not depend on theta */
+    double w = v * ratio;
+    double Pm = Tm * w;
+    double Pb = Pm > 0.0 ? Pm / P->eta_motor : Pm * P->eta_motor;
+    double D = P->voc * P->voc - 4.0 * P->r0 * Pb;
+    double sD = sqrt(D > 0.0 ? D : 0.0);
+    double I = (P->voc - sD) / (2.0 * P->r0);
+    double dI_dR0 = sD > 0.0 ? (2.0 * P->r0 * Pb / sD - (P->voc - sD)) / (2.0 * P->r0 * P->r0) : 0.0;
+    double poly = 0.0; /* fuel map without its scale */
+    if (Te > 0.0) {
+        const double *c = P->fuel_coef;
+        poly = c[0] + c[1] * w + c[2] * Te + c[3] * w * Te + c[4] * w * w + c[5] * Te * Te;
+    }
+    for (int q = 0; q < 5; ++q) {
+        double dI = q == 3 ? dI_dR0 : 0.0;
+        double dmf = q == 4 ? poly : 0.0;
+        g->dt1[q] = ddt[q];
+        g->dxi1[q] = -(ddt[q] * I + o->dt * dI) / P->cap_As;
+        g->dcost[q] = (P->gamma * o->fuel_rate + 1.0 - P->gamma) * ddt[q] + P->gamma * dmf * o->dt;
+    }
+    return 1;
+}
+
+/* Corners, weights and gradient of the trilinear interpolant at a point of a
+ * stage grid (nominal snapping; along a snapped axis the interpolant is flat,
+ * so its slope there is 0).  Returns 0 if the point is outside the grid, 2 if
+ * a corner entering the value or the gradient is infeasible, 1 otherwise. */
+static int interp_grad(const orc_problem *P, int stage, const double *V, double v, double xi, double t,
+                       int64_t corner[8], double wgt[8], double grad[3], int *snapped)
+{
+    const double *nodes[3] = {P->v_nodes + P->v_off[stage], P->xi_nodes + P->xi_off[stage],
+                              P->t_nodes + P->t_off[stage]};
+    int n[3] = {P->nv[stage], P->nxi[stage], P->nt[stage]};
+    double x[3] = {v, xi, t};
+    int i0[3];
+    double f[3], h[3];
+    int snap[3];
+    *snapped = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!locate(nodes[a], n[a], x[a], 0.0, 0.0, NULL, &i0[a], &f[a]))
+            return 0;
+        h[a] = n[a] > 1 ? nodes[a][i0[a] + 1] - nodes[a][i0[a]] : 1.0;
+        /* recompute the raw fraction to know whether it was snapped */
+        double raw = n[a] > 1 ? (fmin(fmax(x[a], nodes[a][0]), nodes[a][n[a] - 1]) - nodes[a][i0[a]]) / h[a] : 0.0;
+        snap[a] = (f[a] != raw);
+        *snapped |= snap[a];
+    }
+    int nv_ = n[0], nx = n[1], nt = n[2];
+    int bad = 0;
+    for (int q = 0; q < 8; ++q) {
+        int a = (q >> 2) & 1, b = (q >> 1) & 1, c = q & 1;
+        int iv = i0[0] + a, ix = i0[1] + b, it = i0[2] + c;
+        if (iv >= nv_)
+            iv = nv_ - 1;
+        if (ix >= nx)
+            ix = nx - 1;
+        if (it >= nt)
+            it = nt - 1;
+        corner[q] = ((int64_t)iv * nx + ix) * nt + it;
+        wgt[q] = (a ? f[0] : 1.0 - f[0]) * (b ? f[1] : 1.0 - f[1]) * (c ? f[2] : 1.0 - f[2]);
+    }
+    for (int a = 0; a < 3; ++a) {
+        grad[a] = 0.0;
+        if (snap[a] || n[a] == 1)
+            continue;
+        for (int q = 0; q < 8; ++q) {
+            int bits[3] = {(q >> 2) & 1, (q >> 1) & 1, q & 1};
+            if (!bits[a])
+                continue;
+            int lo = q & ~(1 << (2 - a));
+            double wo = 1.0; /* weight of the other two axes */
+            for (int o = 0; o < 3; ++o)
+                if (o != a)
+                    wo *= bits[o] ? f[o] : 1.0 - f[o];
+            if (wo == 0.0)
+                continue;
+            double Vh = V[corner[q]], Vl = V[corner[lo]];
+            if (isinf(Vh) || isinf(Vl))
+                bad = 1;
+            else
+                grad[a] += wo * (Vh - Vl) / h[a];
+        }
+    }
+    for (int q = 0; q < 8; ++q)
+        if (wgt[q] != 0.0 && isinf(V[corner[q]]))
+            bad = 1;
+    return bad ? 2 : 1;
+}
+
+/* Forward lambda sweep.  Vall, piall as filled by orc_solve (nominal).
+ * grad[5] receives dJ_0(x0)/dtheta.  diag[4]: number of (stage, state) pairs
+ * on the lambda support, 1 if a snapped fraction was met on the support, 1 if
+ * an infeasible corner entered a value or gradient, the smallest relative gap
+ * (second - best) / |best| of the policy on the support (needs secall, else
+ * NaN).  support (optional, [total states of stages 0..N-1]) receives the
+ * support as 0/1 flags.  Returns ORC_ERR_INFEASIBLE if the support reaches an
+ * infeasible state. */
+int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, const double *secall,
+                const double *x0, double *grad, double *diag, uint8_t *support)
+{
+    int N = P->n_stages;
+    double *lam = calloc((size_t)P->V_off[N + 1], sizeof(double));
+    if (!lam)
+        return ORC_ERR_OOM;
+    for (int q = 0; q < 5; ++q)
+        grad[q] = 0.0;
+    diag[0] = 0;
+    diag[1] = 0;
+    diag[2] = 0;
+    diag[3] = secall ? INFINITY : NAN;
+    /* lambda_0: interpolation weights of x0 on the stage-0 grid */
+    {
+        int64_t cn[8];
+        double wg[8], gr[3];
+        int sn;
+        int rc = interp_grad(P, 0, Vall, x0[0], x0[1], x0[2], cn, wg, gr, &sn);
+        if (rc == 0) {
+            free(lam);
+            return ORC_ERR_INFEASIBLE;
+        }
+        for (int q = 0; q < 8; ++q)
+            if (wg[q] != 0.0)
+                lam[cn[q]] += wg[q];
+    }
+    int status = ORC_OK;
+    for (int k = 0; k < N && status == ORC_OK; ++k) {
+        int nv = P->nv[k], nx = P->nxi[k], nt = P->nt[k];
+        const double *vn = P->v_nodes + P->v_off[k];
+        const double *xn = P->xi_nodes + P->xi_off[k];
+        const double *tn = P->t_nodes + P->t_off[k];
+        int64_t base = P->V_off[k];
+        int64_t n_states = (int64_t)nv * nx * nt;
+        const double *Vn = Vall + P->V_off[k + 1];
+        for (int64_t s = 0; s < n_states; ++s) {
+            double L = lam[base + s];
+            if (L == 0.0)
+                continue;
+            diag[0] += 1;
+            if (support)
+                support[base + s] = 1;
+            int u = piall[base + s];
+            if (u < 0) {
+                status = ORC_ERR_INFEASIBLE;
+                break;
+            }
+            if (secall) {
+                double best = Vall[base + s];
+                double gap = (secall[base + s] - best) / fabs(best);
+                if (gap < diag[3])
+                    diag[3] = gap;
+            }
+            int i = (int)(s / ((int64_t)nx * nt)), j = (int)((s / nt) % nx), l = (int)(s % nt);
+            int bb = u % P->n_b, im = (u / P->n_b) % P->n_tm, ie = u / (P->n_b * P->n_tm);
+            orc_trans tr;
+            orc_dstep dg;
+            if (!transition_grad(P, k, vn[i], xn[j], tn[l], P->te[ie], P->tm[im], bb, &tr, &dg)) {
+                status = ORC_ERR_INFEASIBLE;
+                break;
+            }
+            int64_t cn[8];
+            double wg[8], gr[3];
+            int sn;
+            int rc = interp_grad(P, k + 1, Vn, tr.v1, tr.xi1, tr.t1, cn, wg, gr, &sn);
+            if (rc == 0) {
+                status = ORC_ERR_INFEASIBLE;
+                break;
+            }
+            if (rc == 2)
+                diag[2] = 1;
+            if (sn)
+                diag[1] = 1;
+            for (int q = 0; q < 5; ++q)
+                grad[q] += L * (dg.dcost[q] + gr[0] * dg.dv1[q] + gr[1] * dg.dxi1[q] + gr[2] * dg.dt1[q]);
+            for (int q = 0; q < 8; ++q)
+                if (wg[q] != 0.0)
+                    lam[P->V_off[k + 1] + cn[q]] += L * wg[q];
+        }
+    }
+    free(lam);
+    return status;
+}
+
 /* Cost of a given control sequence from x0 (exact model, no grid): the
  * brute-force pin enumerates sequences with this.  Returns +inf if any step
  * is infeasible or leaves the state box [lo, hi] of the given stage grid. */

@@ -1,0 +1,76 @@
+"""Paper-scale end-to-end parity: the full 100-stage backward sweep and the
+rollout on the GPU against the FP64 oracle's stored results.
+
+The oracle's sweep of this instance (1e11 state x control evaluations) takes
+tens of CPU-core-hours, so `tests/golden/make_c1_golden.py` (which calls only
+the oracle and the seeded generator) stores, for stages 0, 50 and 99, the full
+feasibility masks of the nominal, lenient and strict recursions and the
+values at 8000 seeded states, plus the nominal rollout from x0.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2104_01284_gb300 import problems as P
+from tests._parity import compare
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore")]
+
+torch = pytest.importorskip("torch")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c1_s1.npz")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    if not os.path.exists(GOLDEN):
+        pytest.skip("golden file not generated")
+    return dict(np.load(GOLDEN))
+
+
+@pytest.fixture(scope="module")
+def solved():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_01284_gb300.solver import EcoDP
+    p = P.config1(seed=1)
+    dp = EcoDP(p)
+    dp.solve()
+    torch.cuda.synchronize()
+    yield p, dp
+    dp.close()
+
+
+def _mask(g, name, k, n):
+    return np.unpackbits(g[f"mask_{name}_k{k}"])[:n].astype(bool)
+
+
+@pytest.mark.parametrize("k", [99, 50, 0])
+def test_paper_scale_masks_and_values(golden, solved, k):
+    p, dp = solved
+    n = p.n_states
+    gV = dp.value(k).cpu().numpy().astype(np.float64).ravel()
+    m_nom, m_lo, m_hi = (_mask(golden, nm, k, n) for nm in ("nom", "lo", "hi"))
+    fg = np.isfinite(gV)
+    # (b) mask: equal to nominal except inside the fragile interval
+    diff = fg != m_nom
+    excused = diff & (fg <= m_lo) & (fg >= m_hi)
+    assert not (diff & ~excused).any(), f"k={k}: {int((diff & ~excused).sum())} unexcused mask flips"
+    assert m_nom.sum() > 0.05 * n
+    # (a) values and (c) policy at the stored sample
+    idx = golden[f"idx_k{k}"]
+    gp = dp.policy(k).cpu().numpy().ravel()[idx]
+    st = compare(gV[idx], gp, golden[f"V_nom_k{k}"], golden[f"V_lo_k{k}"], golden[f"V_hi_k{k}"],
+                 golden[f"pi_k{k}"], golden[f"sec_k{k}"], where=f"c1/e2e/k{k}")
+    print(f"k={k}: mask exceptions {int(excused.sum())} of {n}; sample {st}")
+
+
+def test_paper_scale_rollout(golden, solved):
+    p, dp = solved
+    assert int(golden["roll_status"]) == 0
+    r = dp.rollout()
+    assert r["status"] == 0
+    # (d) rollout fuel within 0.1 %
+    assert r["fuel_g"] == pytest.approx(float(golden["roll_fuel_g"]), rel=1e-3)
+    assert r["time_s"] == pytest.approx(float(golden["roll_time_s"]), rel=1e-3)
+    assert r["J"] == pytest.approx(float(golden["roll_J"]), rel=1e-3)
