@@ -185,6 +185,19 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
 dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t k, const float *v_next, float *v_out,
                                 int16_t *pi_out, void *stream);
 
+/* Gradient of the optimal cost J_0(x0) (the interpolated value function at
+ * x0 = {v, soc, t}, host array) with respect to theta = (mass, CdA, Crr, R0,
+ * fuel-map scale), written to the host array dJ_dtheta[5]; J0 (host, may be
+ * NULL) receives J_0(x0).  Envelope theorem: with the stored argmins fixed,
+ * dJ_0/dtheta = sum_k sum_s lam_k(s) (dc/dtheta + grad J_{k+1} . df/dtheta),
+ * with lam propagated forward from x0 through the argmins and the
+ * interpolation weights; the step derivatives follow Eq. (2), (5a), (5b), (6).
+ * FP32 per-state terms, FP64 weights and reduction.  Synchronises the
+ * stream.  DP_ERR_NOT_SOLVED before a solve, DP_ERR_INFEASIBLE if x0 is
+ * outside the grid or infeasible.  The derivative is one-sided information
+ * where an argmin or an interpolation cell changes with theta. */
+dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream);
+
 /* Human-readable name of a status, and the last error message of the
  * calling thread (empty string if none). */
 const char *dp_status_string(dp_status s);

@@ -17,6 +17,9 @@ using namespace ecodp;
 
 namespace ecodp {
 size_t bellman_smem_bytes(const DevParams &hP);
+cudaError_t launch_adjoint(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
+                           size_t stage_elems, const int16_t *piall, size_t pi_elems, double *lam, double x0,
+                           double xi0, double t0, double *out, cudaStream_t s);
 }
 
 namespace {
@@ -63,6 +66,8 @@ struct dp_problem {
     double *d_roll = nullptr;
     int *d_roll_u = nullptr;
     unsigned long long *d_stats = nullptr;
+    double *d_lam = nullptr;  // adjoint weights of two consecutive stages
+    double *d_adj = nullptr;  // adjoint output: gradient[5], J_0(x0), error code, flag
 
     // host copies of the tables (kept until the next update)
     std::vector<float> h_grade, h_cyc, h_red, h_off;
@@ -187,6 +192,7 @@ void fill_params(const dp_problem_desc *d, DevParams &P)
     P.g = f32(d->g);
     P.crr = f32(d->crr);
     P.half_rho_cda = f32(0.5 * d->rho * d->cda);
+    P.half_rho = f32(0.5 * d->rho);
     P.ratio = f32(d->gear / d->r_wheel);
     P.brake_force = f32(d->mass * d->brake_decel);
     P.a_min = f32(d->a_min);
@@ -385,6 +391,8 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, (size_t)(3 * (P.N + 1) + 3 * P.N + 4), &p->d_roll));
     TRY(dev_alloc_n(p, (size_t)P.N, &p->d_roll_u));
     TRY(dev_alloc_n(p, (size_t)4, &p->d_stats));
+    TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_lam));
+    TRY(dev_alloc_n(p, (size_t)8, &p->d_adj));
     TRY(upload_tables(p, p->create_stream));
     auto cuda_try = [&](cudaError_t e, const char *what) -> dp_status {
         if (e != cudaSuccess)
@@ -626,6 +634,31 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
                                 out_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     if (out_is_host)
         DP_CUDA(cudaStreamSynchronize(s));
+    return DP_OK;
+}
+
+dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream)
+{
+    if (!p || !x0 || !dJ_dtheta)
+        return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    if (!finite_all({x0[0], x0[1], x0[2]}))
+        return fail(DP_ERR_INVALID_ARG, "x0 must be finite");
+    if (!p->solved)
+        return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
+    cudaStream_t s = (cudaStream_t)stream;
+    DP_CUDA(launch_adjoint(p->dP, p->hP, p->tables(), p->d_V, p->stage_elems, p->d_pi, p->pi_elems, p->d_lam, x0[0],
+                           x0[1], x0[2], p->d_adj, s));
+    double h[8];
+    DP_CUDA(cudaMemcpyAsync(h, p->d_adj, sizeof h, cudaMemcpyDeviceToHost, s));
+    DP_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < 5; ++q)
+        dJ_dtheta[q] = h[q];
+    if (J0)
+        *J0 = h[5];
+    if (h[6] == 1.0 || h[6] == 2.0 || !(h[5] < 1e12))
+        return fail(DP_ERR_INFEASIBLE, "x0 is outside the grid or infeasible");
+    if (h[6] == 3.0)
+        return fail(DP_ERR_INTERNAL, "the adjoint support reached an infeasible state");
     return DP_OK;
 }
 

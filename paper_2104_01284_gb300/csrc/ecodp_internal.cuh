@@ -50,6 +50,7 @@ struct DevParams {
     float ds;
     // model
     float mass, g, crr, half_rho_cda, ratio, brake_force, a_min, a_max, eta, voc, r0, cap;
+    float half_rho;  // rho / 2 (for the CdA derivative of the adjoint)
     float fc[6];
     float fuel_scale, gamma;
     float soc_ref, w_soc, v_ref, w_v;

@@ -107,3 +107,7 @@ def check(status: int, where: str):
 # allocation-free single stage (static device working memory)
 dp_solve_stage_static = _sig("dp_solve_stage_static", C.POINTER(ProblemDesc), C.c_int32, vp, vp, vp, vp)
 EXPORTED.append("dp_solve_stage_static")
+
+# adjoint dJ_0(x0)/dtheta, theta = (mass, CdA, Crr, R0, fuel_scale)
+dp_adjoint = _sig("dp_adjoint", vp, dbl_p, dbl_p, dbl_p, vp)
+EXPORTED.append("dp_adjoint")

@@ -173,6 +173,18 @@ class EcoDP:
                                      _stream_handle(stream)), "dp_solve_stage")
         return vo, po
 
+    def adjoint(self, x0=None, stream=None):
+        """(J_0(x0), dJ_0(x0)/dtheta) for theta = THETA, by the envelope
+        theorem on the stored solution.  Returns (float, numpy[5])."""
+        x = np.array(self.p.x0 if x0 is None else x0, dtype=np.float64)
+        g = np.zeros(5)
+        J = C.c_double(0.0)
+        with torch.cuda.device(self.device):
+            N.check(N.dp_adjoint(self.h, x.ctypes.data_as(C.POINTER(C.c_double)),
+                                 g.ctypes.data_as(C.POINTER(C.c_double)), C.byref(J), _stream_handle(stream)),
+                    "dp_adjoint")
+        return J.value, g
+
     def rollout(self, x0=None, stream=None, raise_infeasible: bool = True):
         """Forward rollout from x0 (default p.x0); returns numpy arrays."""
         n = self.n_stages
@@ -191,3 +203,44 @@ class EcoDP:
         out["traj"] = np.stack([bufs["v"], bufs["soc"], bufs["t"]], axis=1)
         out.update(fuel_g=tr.fuel_g, time_s=tr.time_s, J=tr.J, fail_stage=tr.fail_stage, status=st)
         return out
+
+
+THETA = ("mass", "cda", "crr", "r0", "fuel_scale")
+_SOLVERS = {}
+
+
+def _solver_for(p, device):
+    """A cached EcoDP for problems of p's sizes on device (re-used through
+    dp_problem_update, so repeated evaluations do not reallocate)."""
+    key = (str(device), p.n_stages, p.n_v, p.n_soc, p.n_t, p.n_te, p.n_tm, p.n_brake, len(p.light_stage),
+           p.te_lo, p.te_hi, p.tm_lo, p.tm_hi)
+    dp = _SOLVERS.get(key)
+    if dp is None:
+        dp = EcoDP(p, device=device)
+        _SOLVERS[key] = dp
+    else:
+        dp.update(p)
+    return dp
+
+
+class EcoDPValue(torch.autograd.Function):
+    """J_0(x0; theta), the optimal cost of problem p at x0, as a function of
+    theta = (mass, CdA, Crr, R0, fuel_scale) (a float64 tensor of 5).  The
+    forward pass solves the backward recursion on the GPU; the backward pass
+    returns the adjoint gradient (dp_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, theta, p, x0=None, device=None):
+        th = theta.detach().to("cpu", torch.float64).tolist()
+        q = p.replace(**dict(zip(THETA, th)))
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        dp = _solver_for(q, dev)
+        dp.solve()
+        J, g = dp.adjoint(x0)
+        ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+        return torch.tensor(J, dtype=theta.dtype, device=theta.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return grad_out * g, None, None, None
