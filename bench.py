@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload (0: skip it)")
     return ap.parse_args()
 
 
@@ -199,6 +200,69 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(n_inst, dev, stream, steps=2):
+    """Batched uneven instances (256 seeded horizons of 20-150 stages, 31-61
+    speeds, 31-51 SoC points, 101-251 times, 21x21-31x31 torques x brake,
+    1-6 lights) in one persistent launch under a CUDA graph, with the tile
+    configuration picked by the autotuner on the first 32 instances; against
+    the same instances solved one at a time by the single-problem path (its
+    own CUDA graph per instance, on one stream).  Inputs are far larger than
+    L2 (tens of GB), so no flush is needed between steps."""
+    import torch
+
+    from paper_2104_01284_gb300 import problems as P
+    from paper_2104_01284_gb300.solver import EcoDP, EcoDPBatch
+    probs = P.config3_batch(seed=3, n_instances=n_inst)
+    with torch.cuda.stream(stream):
+        with EcoDPBatch(probs[:min(32, n_inst)], device=dev, stream=stream) as tune:
+            best = tune.autotune(repeats=1, stream=stream)
+        bt = EcoDPBatch(probs, device=dev, stream=stream, rows_per_lane=best["rows_per_lane"],
+                        ctas_per_sm=best["ctas_per_sm"])
+        bt.solve(stream)
+        bt.wait(stream)
+        times = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.solve(stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        bt.wait(stream)
+        prof = bt.profile(stream)
+        info = bt.info()
+        bt.close()
+        # the same instances through the single-problem path, one at a time
+        single_ms = 0.0
+        for c0 in range(0, n_inst, 32):
+            dps = [EcoDP(q, device=dev, stream=stream) for q in probs[c0:c0 + 32]]
+            for d in dps:
+                d.solve(stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for d in dps:
+                d.solve(stream)
+            e1.record(stream)
+            e1.synchronize()
+            single_ms += e0.elapsed_time(e1)
+            for d in dps:
+                d.close()
+    ms = statistics.median(times)
+    return {"workload": f"{n_inst} uneven instances (config-3 family, seed 3)", "instances": n_inst,
+            "solves_per_s": n_inst / (ms / 1e3), "ms_per_batch": ms,
+            "nominal_evals_per_s": info["nominal_evals"] / (ms / 1e3),
+            "single_path_solves_per_s": n_inst / (single_ms / 1e3), "single_path_ms": single_ms,
+            "speedup_vs_single_path": single_ms / ms,
+            "tile_config": {"rows_per_lane": best["rows_per_lane"], "ctas_per_sm": best["ctas_per_sm"],
+                            "autotune_ms_on_32": best["ms"]},
+            "persistent_ms": prof["bellman"], "precompute_ms": prof["precompute"],
+            "work_items": info["work_items"], "ctas": info["ctas"], "device_gb": info["device_bytes"] / 1e9,
+            "gpu_launches_per_batch": 3, "steps": steps}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -293,6 +357,17 @@ def run_ours(args):
            "h2d_bytes_per_step": int(stats["h2d_update_bytes"]), "d2h_bytes_per_step": int(stats["d2h_rollout_bytes"]),
            "ms_per_step": 1e3 * float(te.item()) / args.steps}
 
+    # adjoint dJ*/dtheta at x0 on the solved instance (host-synchronous call)
+    dp.solve(stream)
+    dp.adjoint(stream=stream)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        J0, grad = dp.adjoint(stream=stream)
+    adjoint = {"ms_per_call": 1e3 * (time.perf_counter() - t0) / 3, "J0": J0,
+               "dJ_dtheta": dict(zip(("mass", "cda", "crr", "r0", "fuel_scale"), map(float, grad)))}
+
+    batched = bench_batched(args.batch, dev, stream) if args.batch > 0 else None
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -301,7 +376,7 @@ def run_ours(args):
         "effective_evals_per_s": world * stats["effective_evals"] * args.steps / (total_ms / 1e3),
         "rollout": {"fuel_g": traj["fuel_g"], "time_s": traj["time_s"], "J": traj["J"]},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks,
+        "clocks": clocks, "adjoint": adjoint, "batched": batched,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)

@@ -232,6 +232,85 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4]);
  * kernel recovered.  DP_ERR_NOT_SOLVED before a sweep. */
 dp_status dp_sweep_stats(dp_problem_t p, int64_t out[6], void *stream);
 
+/* ---- Batches of independent problems ------------------------------------
+ *
+ * The paper solves one horizon at a time (Sec. IV-V).  A batch solves many
+ * independent problems -- each its own recursion of Eq. (9a)-(9d), with its
+ * own horizon, grids, controls and lights -- in one persistent Bellman
+ * launch.  Every instance's values and policies are bit-identical to those
+ * of dp_solve_backward on the same descriptor (same arithmetic, same tie
+ * order), whatever the batch and the configuration.  A batch owns the device
+ * memory of all its instances (through the caller's allocator when one is
+ * given) until dp_multi_destroy.  After DP_ERR_CUDA the batch must only be
+ * destroyed. */
+typedef struct dp_multi *dp_multi_t;
+
+typedef struct dp_multi_opts {
+    int32_t rows_per_lane; /* SoC rows per lane of a Bellman tile: 4 or 8 (0 = 8) */
+    int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent launch (0 = as many as fit) */
+} dp_multi_opts;
+
+/* Validate descs[0..n-1] (the rules of dp_problem_create, instance by
+ * instance), allocate every instance's value function, policy and per-stage
+ * tables, and upload the route tables on `stream` (synchronised before
+ * returning).  opts may be NULL (defaults).  Errors: DP_ERR_INVALID_ARG (the
+ * message names the instance), DP_ERR_OOM, DP_ERR_CUDA. */
+dp_status dp_multi_create(const dp_problem_desc *descs, int32_t n, const dp_multi_opts *opts,
+                          const dp_allocator *alloc, void *stream, dp_multi_t *out);
+
+/* Free everything.  NULL is accepted. */
+dp_status dp_multi_destroy(dp_multi_t m);
+
+/* Change the tile configuration (rows_per_lane in {0, 4, 8}, ctas_per_sm in
+ * [0, the number that fit]); synchronises the creation stream.  Results of
+ * earlier solves become stale (DP_ERR_NOT_SOLVED). */
+dp_status dp_multi_set_config(dp_multi_t m, int32_t rows_per_lane, int32_t ctas_per_sm);
+
+/* Solve every instance: terminal values and per-stage tables of all
+ * instances (one launch each), then one persistent launch over (instance,
+ * stage, tile) work items in wavefront order, each tile of stage k waiting
+ * for the tiles of stage k+1 of its instance.  The launches are captured in
+ * a CUDA graph on the first call (and after dp_multi_set_config) and replayed
+ * on `stream`.  Asynchronous; a dependency wait that gives up (after 10 s) is
+ * reported by the next synchronising call as DP_ERR_TIMEOUT. */
+dp_status dp_multi_solve(dp_multi_t m, void *stream);
+
+/* Synchronise `stream` and report DP_ERR_TIMEOUT if the last solve's
+ * persistent launch gave up a dependency wait. */
+dp_status dp_multi_wait(dp_multi_t m, void *stream);
+
+/* One solve with direct launches and CUDA events (same work and results as
+ * dp_multi_solve); synchronises and reports ms[0] terminal + precompute
+ * launches, ms[1] the persistent Bellman launch, ms[2] the whole solve. */
+dp_status dp_multi_profile(dp_multi_t m, void *stream, float ms[3]);
+
+/* Autotuner: time every configuration (rows_per_lane in {4, 8} x every
+ * ctas_per_sm that fits), `repeats` timed solves each after one warm-up,
+ * keep the fastest (minimum whole-solve time) and set it.  best[0] =
+ * rows_per_lane, best[1] = ctas_per_sm; *best_ms (may be NULL) its time.
+ * Synchronises; leaves the batch solved. */
+dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t best[2], float *best_ms);
+
+/* out[0] instances, out[1] work items of the persistent launch, out[2] its
+ * CTAs, out[3] rows_per_lane, out[4] CTAs per SM, out[5] nominal state x
+ * control evaluations of one solve (sum of N n_v n_soc n_t n_controls),
+ * out[6] device bytes held, out[7] the longest horizon. */
+dp_status dp_multi_info(dp_multi_t m, int64_t out[8]);
+
+/* J_stage / pi_stage of instance b, as dp_get_value / dp_get_policy (dense
+ * [n_v][n_soc][n_t] of that instance, device or host memory as flagged).
+ * Synchronise the stream. */
+dp_status dp_multi_get_value(dp_multi_t m, int32_t b, int32_t stage, float *out, int32_t out_is_host, void *stream);
+dp_status dp_multi_get_policy(dp_multi_t m, int32_t b, int32_t stage, int16_t *out, int32_t out_is_host,
+                              void *stream);
+
+/* Forward rollout of every instance (one CTA each, the arithmetic of
+ * dp_rollout): x0 is a host array [n][3], traj an array of n caller-owned
+ * trajectories sized for their instances.  Synchronises.  DP_ERR_INFEASIBLE
+ * if any instance has a stage without a feasible control (every
+ * trajectory's fail_stage tells which). */
+dp_status dp_multi_rollout(dp_multi_t m, const double *x0, dp_trajectory *traj, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,21 +10,22 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ecodp.h"
-#include "ecodp_internal.cuh"
+#include "api_internal.h"
 
 using namespace ecodp;
+using namespace ecodp::host;
 
 namespace ecodp {
 size_t bellman_smem_bytes(const DevParams &hP);
 cudaError_t launch_adjoint(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
                            size_t stage_elems, const int16_t *piall, size_t pi_elems, double *lam, double x0,
                            double xi0, double t0, double *out, cudaStream_t s);
-}
+
+namespace host {
 
 namespace {
-
 thread_local std::string g_last_error;
+}
 
 dp_status fail(dp_status s, const std::string &msg)
 {
@@ -32,14 +33,10 @@ dp_status fail(dp_status s, const std::string &msg)
     return s;
 }
 
-#define DP_CUDA(call)                                                                             \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
-            return fail(DP_ERR_CUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
-    } while (0)
+const char *last_error() { return g_last_error.c_str(); }
 
-}  // namespace
+}  // namespace host
+}  // namespace ecodp
 
 struct dp_problem {
     int N = 0, n_v = 0, n_xi = 0, n_t = 0, n_u = 0, n_lights = 0;
@@ -69,9 +66,7 @@ struct dp_problem {
     double *d_lam = nullptr;  // adjoint weights of two consecutive stages
     double *d_adj = nullptr;  // adjoint output: gradient[5], J_0(x0), error code, flag
 
-    // host copies of the tables (kept until the next update)
-    std::vector<float> h_grade, h_cyc, h_red, h_off;
-    std::vector<int> h_lon;
+    HostTables h;  // host copies of the tables (kept until the next update)
 
     bool solved = false;
     int variant = 1;
@@ -85,7 +80,8 @@ struct dp_problem {
     int16_t *pi(int k) const { return d_pi + (size_t)k * pi_elems; }
 };
 
-namespace {
+namespace ecodp {
+namespace host {
 
 bool finite_all(std::initializer_list<double> xs)
 {
@@ -152,7 +148,9 @@ dp_status validate(const dp_problem_desc *d)
     return DP_OK;
 }
 
+namespace {
 float f32(double x) { return (float)x; }
+}  // namespace
 
 void fill_params(const dp_problem_desc *d, DevParams &P)
 {
@@ -211,23 +209,31 @@ void fill_params(const dp_problem_desc *d, DevParams &P)
     P.w_v = f32(d->w_v);
 }
 
-void fill_tables(const dp_problem_desc *d, dp_problem *p)
+void fill_tables(const dp_problem_desc *d, HostTables &t)
 {
-    p->h_grade.assign(d->n_stages, 0.f);
+    t.grade.assign(d->n_stages, 0.f);
     for (int q = 0; q < d->n_stages; ++q)
-        p->h_grade[q] = f32(d->grade[q]);
+        t.grade[q] = f32(d->grade[q]);
     int nl = d->n_lights;
-    p->h_cyc.assign(nl > 0 ? nl : 1, 1.f);
-    p->h_red.assign(nl > 0 ? nl : 1, 0.f);
-    p->h_off.assign(nl > 0 ? nl : 1, 0.f);
-    p->h_lon.assign(d->n_stages + 1, -1);
+    t.cyc.assign(nl > 0 ? nl : 1, 1.f);
+    t.red.assign(nl > 0 ? nl : 1, 0.f);
+    t.off.assign(nl > 0 ? nl : 1, 0.f);
+    t.lon.assign(d->n_stages + 1, -1);
     for (int q = 0; q < nl; ++q) {
-        p->h_cyc[q] = f32(d->cycle[q]);
-        p->h_red[q] = f32(d->red[q]);
-        p->h_off[q] = f32(d->offset[q]);
-        p->h_lon[d->light_stage[q]] = q;
+        t.cyc[q] = f32(d->cycle[q]);
+        t.red[q] = f32(d->red[q]);
+        t.off[q] = f32(d->offset[q]);
+        t.lon[d->light_stage[q]] = q;
     }
 }
+
+bool finite3(const double x[3]) { return finite_all({x[0], x[1], x[2]}); }
+
+}  // namespace host
+}  // namespace ecodp
+
+namespace {
+
 
 dp_status dev_alloc(dp_problem *p, size_t bytes, void **out)
 {
@@ -281,12 +287,12 @@ void release(dp_problem *p)
 dp_status upload_tables(dp_problem *p, cudaStream_t s)
 {
     DP_CUDA(cudaMemcpyAsync(p->dP, &p->hP, sizeof(DevParams), cudaMemcpyHostToDevice, s));
-    DP_CUDA(cudaMemcpyAsync(p->d_grade, p->h_grade.data(), p->h_grade.size() * sizeof(float),
+    DP_CUDA(cudaMemcpyAsync(p->d_grade, p->h.grade.data(), p->h.grade.size() * sizeof(float),
                             cudaMemcpyHostToDevice, s));
-    DP_CUDA(cudaMemcpyAsync(p->d_lon, p->h_lon.data(), p->h_lon.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    DP_CUDA(cudaMemcpyAsync(p->d_cyc, p->h_cyc.data(), p->h_cyc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-    DP_CUDA(cudaMemcpyAsync(p->d_red, p->h_red.data(), p->h_red.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-    DP_CUDA(cudaMemcpyAsync(p->d_off, p->h_off.data(), p->h_off.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_lon, p->h.lon.data(), p->h.lon.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_cyc, p->h.cyc.data(), p->h.cyc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_red, p->h.red.data(), p->h.red.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    DP_CUDA(cudaMemcpyAsync(p->d_off, p->h.off.data(), p->h.off.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     return DP_OK;
 }
 
@@ -323,7 +329,7 @@ const char *dp_status_string(dp_status s)
     return "DP_ERR_UNKNOWN";
 }
 
-const char *dp_last_error(void) { return g_last_error.c_str(); }
+const char *dp_last_error(void) { return last_error(); }
 
 dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *alloc, void *stream, dp_problem_t *out)
 {
@@ -344,7 +350,7 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
         p->has_alloc = true;
     }
     fill_params(desc, p->hP);
-    fill_tables(desc, p);
+    fill_tables(desc, p->h);
     p->N = desc->n_stages;
     p->n_v = desc->n_v;
     p->n_xi = desc->n_soc;
@@ -367,11 +373,11 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
         }                   \
     } while (0)
     TRY(dev_alloc_n(p, 1, &p->dP));
-    TRY(dev_alloc_n(p, p->h_grade.size(), &p->d_grade));
-    TRY(dev_alloc_n(p, p->h_lon.size(), &p->d_lon));
-    TRY(dev_alloc_n(p, p->h_cyc.size(), &p->d_cyc));
-    TRY(dev_alloc_n(p, p->h_red.size(), &p->d_red));
-    TRY(dev_alloc_n(p, p->h_off.size(), &p->d_off));
+    TRY(dev_alloc_n(p, p->h.grade.size(), &p->d_grade));
+    TRY(dev_alloc_n(p, p->h.lon.size(), &p->d_lon));
+    TRY(dev_alloc_n(p, p->h.cyc.size(), &p->d_cyc));
+    TRY(dev_alloc_n(p, p->h.red.size(), &p->d_red));
+    TRY(dev_alloc_n(p, p->h.off.size(), &p->d_off));
     TRY(dev_alloc_n(p, p->stage_elems * (size_t)(p->N + 1), &p->d_V));
     TRY(dev_alloc_n(p, p->pi_elems * (size_t)p->N, &p->d_pi));
     if (P.n_cls > MAX_CLASSES) {
@@ -431,7 +437,7 @@ dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *s
     if (P.n_cls != p->hP.n_cls)
         return fail(DP_ERR_INVALID_ARG, "update changes the torque class structure");
     p->hP = P;
-    fill_tables(desc, p);
+    fill_tables(desc, p->h);
     st = upload_tables(p, (cudaStream_t)stream);
     p->solved = false;
     return st;
@@ -471,8 +477,7 @@ dp_status dp_sweep_stats(dp_problem_t p, int64_t out[6], void *stream)
     out[0] = (int64_t)h[0] * p->n_xi * p->n_t;
     out[1] = (int64_t)h[1] * p->n_xi * p->n_t;
     // bytes of one dp_problem_update (tables) and one dp_rollout (trajectory)
-    out[2] = (int64_t)(sizeof(DevParams) + p->h_grade.size() * sizeof(float) + p->h_lon.size() * sizeof(int) +
-                       3 * p->h_cyc.size() * sizeof(float));
+    out[2] = (int64_t)(sizeof(DevParams) + p->h.bytes());
     out[3] = (int64_t)((3 * (p->N + 1) + 3 * p->N + 4) * sizeof(double) + p->N * sizeof(int));
     out[4] = (int64_t)h[2];
     out[5] = (int64_t)h[3];

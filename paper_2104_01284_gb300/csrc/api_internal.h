@@ -1,0 +1,45 @@
+// Host helpers shared by the translation units of the C ABI (api.cu for
+// single problems, api_multi.cu for batches and the serving loop).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/ecodp.h"
+#include "ecodp_internal.cuh"
+
+namespace ecodp {
+namespace host {
+
+// Record msg as the calling thread's last error and return s.
+dp_status fail(dp_status s, const std::string &msg);
+
+// Range checks of a problem descriptor (the limits documented in ecodp.h).
+dp_status validate(const dp_problem_desc *d);
+
+// Sizes, grids and FP32 model constants of a descriptor.
+void fill_params(const dp_problem_desc *d, DevParams &P);
+
+// Per-stage route tables in the layout of StageTables.
+struct HostTables {
+    std::vector<float> grade, cyc, red, off;
+    std::vector<int> lon;  // light index of each node, -1 = none
+    size_t bytes() const
+    {
+        return grade.size() * sizeof(float) + lon.size() * sizeof(int) + 3 * cyc.size() * sizeof(float);
+    }
+};
+void fill_tables(const dp_problem_desc *d, HostTables &t);
+
+bool finite3(const double x[3]);
+const char *last_error();
+
+}  // namespace host
+}  // namespace ecodp
+
+#define DP_CUDA(call)                                                                                           \
+    do {                                                                                                        \
+        cudaError_t e_ = (call);                                                                                \
+        if (e_ != cudaSuccess)                                                                                  \
+            return ::ecodp::host::fail(DP_ERR_CUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
+    } while (0)

@@ -1,0 +1,467 @@
+// Device code of one Bellman tile, shared by the single-problem kernel
+// (k_bellman.cu) and the batched persistent kernel (k_batch.cu).
+//
+// J_k(v_i, xi_j, t_l) = min_u [c + J_{k+1}(f(x, u))] and its argmin
+// (Eq. 9b-9d).  For control u in torque class C (same T_eng + T_bsg and brake
+// flag) the successor is (v'_C, xi_j - dxi_u, t_l + dt_C): the speed and time
+// axes of the trilinear interpolation are shared by the class and only the
+// SoC axis depends on u (Eq. 5a-5c).  With uniform grids the SoC shift is the
+// same for every j and the time shift the same for every l, so
+//   J_{k+1}(f(x, u)) = w0_u G_C(j + d_u) + w1_u G_C(j + d_u + 1)
+// where G_C(j') blends two speed rows and two time columns of J_{k+1} at SoC
+// row j'.  G_C is computed once per class and lane; the per-control work is
+// two FMAs and one min.  At a light stage the arrival check (Eq. 5c, 7c, 8)
+// depends on the arrival time (per lane and class); on the standstill row
+// v = 0 at a light node the departure waits for green, which shifts the time
+// landing per time node.
+//
+// A tile is one speed row and TLANES lanes; each lane owns one (SoC group of
+// R rows, time node) pair, the pairs of a row laid out back to back so no lane
+// idles on a ragged time axis.  The row's class and control tables are staged
+// in shared memory.  Per class a lane keeps a register window of R + 4
+// blended values; the controls of a class are grouped by SoC shift
+// d in {-2, -1, 0, 1} so window offsets are compile-time constants; two rows go
+// through one packed FP32 FMA (__ffma2_rn) and two controls through one
+// three-input min.  Only class minima are tracked in the sweep; afterwards each
+// warp buckets its states by winning class in shared memory and re-evaluates
+// that class (bit for bit the same arithmetic) to recover the argmin.
+//
+// Argmin order: (value, torque class, control index).  Among controls with
+// exactly equal FP32 values the first class in class order (total torque
+// ascending, brake flag fastest) wins, then the lowest control index inside
+// it.  Exact FP32 ties are rounding coincidences of near-equal costs (the
+// FP64 recursion has none on the seeded instances); resolving them toward the
+// lowest global control index would re-evaluate every tied class.
+#pragma once
+
+#include <climits>
+
+#include "ecodp_internal.cuh"
+
+namespace ecodp {
+namespace tile {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int TW = 4;  // warps per tile
+constexpr int TLANES = TW * 32;
+
+// Loads of J_{k+1}: through the read-only path when J_{k+1} cannot change
+// during the launch (one stage per launch), through L1/L2 otherwise (a
+// persistent launch whose other CTAs wrote it, ordered by an acquire).
+template <bool NC>
+__device__ __forceinline__ float ldv(const float *p)
+{
+    if (NC)
+        return __ldg(p);
+    return __ldca(p);
+}
+
+template <bool NC>
+__device__ __forceinline__ float blend(const float *p0, const float *p1, float wv0, float wv1, float wt0, float wt1)
+{
+    float A = __fmaf_rn(wv1, ldv<NC>(p1), __fmul_rn(wv0, ldv<NC>(p0)));
+    float B = __fmaf_rn(wv1, ldv<NC>(p1 + 1), __fmul_rn(wv0, ldv<NC>(p0 + 1)));
+    return __fmaf_rn(wt1, B, __fmul_rn(wt0, A));
+}
+
+// Per-lane interpolation context of one class.
+struct TCtx {
+    const float *p0, *p1;  // speed rows iv, iv+1 of J_{k+1} at padded SoC row 0, lower time column
+    float wv0, wv1, wt0, wt1;
+    bool red;              // arrival during red: every value of the class is infeasible
+};
+
+struct StageInfo {
+    bool wait_row;   // v_i == 0 at a light node: wait for green before departing
+    int next_light;  // light index at node k+1, or -1
+    float cyc1, red1, off1;
+};
+
+__device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, const ClassRec &C, int l, float tl,
+                                          float wait, const StageInfo &si)
+{
+    TCtx x;
+    int t0;
+    float ft;
+    if (!si.wait_row) {
+        t0 = l + C.st;
+        ft = C.ft;
+    } else {
+        int st;
+        snap_split(__fdiv_rn(__fadd_rn(wait, C.dt), P.h_t), st, ft);
+        t0 = l + st;
+    }
+    // a lower corner past the grid reads the padding column n_t; the upper
+    // corner is the next column, still inside the row (ld_t >= n_t + 2)
+    const int ta = min(t0, P.n_t);
+    x.wt1 = ft;
+    x.wt0 = __fsub_rn(1.f, ft);
+    x.wv1 = C.fv;
+    x.wv0 = __fsub_rn(1.f, C.fv);
+    const size_t vrow = (size_t)P.xi_rows * P.ld_t;
+    x.p0 = Vn + (size_t)C.iv * vrow + ta;
+    x.p1 = x.p0 + vrow;
+    x.red = false;
+    if (si.next_light >= 0 && C.v1 > 0.f) {
+        float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
+        x.red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
+    }
+    return x;
+}
+
+__device__ __forceinline__ int row_offset(const DevParams &P, int j)
+{
+    return (min(max(j, -1), P.n_xi) + 1) * P.ld_t;
+}
+
+// Blended value G at SoC row j (any integer; rows outside the grid read padding).
+template <bool NC>
+__device__ __forceinline__ float g_at(const DevParams &P, const TCtx &x, int j)
+{
+    const int o = row_offset(P, j);
+    const float g = blend<NC>(x.p0 + o, x.p1 + o, x.wv0, x.wv1, x.wt0, x.wt1);
+    return x.red ? V_BIG : g;
+}
+
+// c + w0 g0 + w1 g1, in this order (the packed path rounds identically).
+__device__ __forceinline__ float split_value(const SplitRec &S, float g0, float g1)
+{
+    return __fmaf_rn(S.w1, g1, __fmaf_rn(S.w0, g0, S.c));
+}
+
+__device__ __forceinline__ int split_u(const SplitRec &S) { return (int)(S.bits & 0xffffu); }
+__device__ __forceinline__ int split_d(const SplitRec &S) { return (int)(short)(S.bits >> 16); }
+
+__device__ __forceinline__ float min3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ StageInfo stage_info(const StageTables &tb, int k, float v)
+{
+    StageInfo si;
+    int lk = tb.light_of_node[k];
+    si.wait_row = (lk >= 0) && (v == 0.f);
+    si.next_light = tb.light_of_node[k + 1];
+    si.cyc1 = si.red1 = si.off1 = 0.f;
+    if (si.next_light >= 0) {
+        si.cyc1 = tb.cycle[si.next_light];
+        si.red1 = tb.red[si.next_light];
+        si.off1 = tb.offset[si.next_light];
+    }
+    return si;
+}
+
+// Standstill time at a red light before departing from (v = 0, t) at node k.
+__device__ __forceinline__ float wait_time(const StageTables &tb, int k, float tl, bool wait_row)
+{
+    if (!wait_row)
+        return 0.f;
+    int lk = tb.light_of_node[k];
+    float ph = phase_pos(tl, tb.offset[lk], tb.cycle[lk]);
+    float r = tb.red[lk];
+    return ph < r ? __fsub_rn(r, ph) : 0.f;
+}
+
+// Minimum over the controls of one SoC-shift bucket: row r uses window values
+// G[r + D + 2] and G[r + D + 3].  EV holds the even-aligned pairs
+// {G[2p], G[2p+1]}, OD the odd-aligned pairs {G[2p+1], G[2p+2]}.
+template <int R, int D>
+__device__ __forceinline__ void bucket_min(const SplitRec *spl, int q, int n, const float2 (&EV)[R / 2 + 2],
+                                           const float2 (&OD)[R / 2 + 1], float (&cm)[R])
+{
+    const int end = q + n;
+    for (; q + 1 < end; q += 2) {
+        const SplitRec s1 = spl[q], s2 = spl[q + 1];
+        const float2 c1 = make_float2(s1.c, s1.c), w01 = make_float2(s1.w0, s1.w0), w11 = make_float2(s1.w1, s1.w1);
+        const float2 c2 = make_float2(s2.c, s2.c), w02 = make_float2(s2.w0, s2.w0), w12 = make_float2(s2.w1, s2.w1);
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) {
+            const float2 LO = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 HI = ((D & 1) == 0) ? OD[p + (D + 2) / 2] : EV[p + (D + 3) / 2];
+            const float2 F1 = __ffma2_rn(w11, HI, __ffma2_rn(w01, LO, c1));
+            const float2 F2 = __ffma2_rn(w12, HI, __ffma2_rn(w02, LO, c2));
+            cm[2 * p] = min3(cm[2 * p], F1.x, F2.x);
+            cm[2 * p + 1] = min3(cm[2 * p + 1], F1.y, F2.y);
+        }
+    }
+    if (q < end) {
+        const SplitRec s1 = spl[q];
+        const float2 c1 = make_float2(s1.c, s1.c), w01 = make_float2(s1.w0, s1.w0), w11 = make_float2(s1.w1, s1.w1);
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) {
+            const float2 LO = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 HI = ((D & 1) == 0) ? OD[p + (D + 2) / 2] : EV[p + (D + 3) / 2];
+            const float2 F1 = __ffma2_rn(w11, HI, __ffma2_rn(w01, LO, c1));
+            cm[2 * p] = fminf(cm[2 * p], F1.x);
+            cm[2 * p + 1] = fminf(cm[2 * p + 1], F1.y);
+        }
+    }
+}
+
+// Lowest control index of class E whose value at SoC row j equals bv (INT_MAX
+// if none), re-evaluated with exactly the arithmetic of the sweep.
+template <bool NC>
+__device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x, const ClassEntry &E,
+                                              const SplitRec *spl, int j, float bv)
+{
+    float g5[5];  // SoC rows j - 2 .. j + 2
+#pragma unroll
+    for (int w = 0; w < 5; ++w)
+        g5[w] = g_at<NC>(P, x, j - 2 + w);
+    int ub = INT_MAX;
+    int q = E.off;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {  // bucket b holds the shift d = b - 2
+        for (int n = 0; n < E.nb[b]; ++n, ++q) {
+            const SplitRec S = spl[q];
+            const int u = split_u(S);
+            if (split_value(S, g5[b], g5[b + 1]) == bv && u < ub)
+                ub = u;
+        }
+    }
+    for (int n = 0; n < E.n_other; ++n, ++q) {
+        const SplitRec S = spl[q];
+        const int d = split_d(S), u = split_u(S);
+        if (split_value(S, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv && u < ub)
+            ub = u;
+    }
+    return ub;
+}
+
+// Shared memory of a tile: the row's tables, then per warp the argmin-recovery
+// buffers: counters [n_cls + 1], entry list [32 R], best value per state [32 R].
+struct Layout {
+    size_t ent, spl, warp, warp_bytes, total;
+    size_t w_list, w_best;  // offsets inside a warp's block
+};
+
+template <int R>
+__host__ __device__ inline Layout layout(int n_cls, int n_u)
+{
+    Layout L;
+    size_t o = (size_t)n_cls * sizeof(ClassRec);
+    L.ent = o;
+    o += (size_t)n_cls * sizeof(ClassEntry);
+    L.spl = o;
+    o += (size_t)n_u * sizeof(SplitRec);
+    L.warp = o;
+    size_t w = ((size_t)(n_cls + 1) * sizeof(int) + 15) / 16 * 16;
+    L.w_list = w;
+    w += (size_t)32 * R * sizeof(unsigned);
+    L.w_best = w;
+    w += (size_t)32 * R * sizeof(float);
+    L.warp_bytes = w;
+    L.total = o + TW * L.warp_bytes;
+    return L;
+}
+
+// Flattened (SoC group, time) lanes of one speed row.
+template <int R>
+__host__ __device__ inline int chunks_per_row(int n_xi, int n_t)
+{
+    return ((n_xi + R - 1) / R * n_t + TLANES - 1) / TLANES;
+}
+
+// One tile: speed row i, lane chunk `chunk` of stage k.  The row's tables
+// are (cls, ent, spl) with n_ent feasible classes and n_spl controls.  All
+// TLANES threads of the CTA must call it; it starts and ends with a barrier
+// so the shared memory can be reused by the next tile.
+template <int R, bool NC>
+__device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, const ClassRec *g_cls,
+                             const ClassEntry *g_ent, const SplitRec *g_spl, int n_ent, int n_spl, const float *Vn,
+                             float *__restrict__ Vk, int16_t *__restrict__ pik, int i, int chunk,
+                             unsigned char *smem_raw, unsigned long long *stats)
+{
+    const int tid = threadIdx.x;
+    const Layout L = layout<R>(P.n_cls, P.n_u);
+    ClassRec *s_cls = reinterpret_cast<ClassRec *>(smem_raw);
+    ClassEntry *s_ent = reinterpret_cast<ClassEntry *>(smem_raw + L.ent);
+    SplitRec *s_spl = reinterpret_cast<SplitRec *>(smem_raw + L.spl);
+    __syncthreads();  // the previous tile may still read the tables
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(g_cls);
+        int4 *dst = reinterpret_cast<int4 *>(s_cls);
+        for (int q = tid; q < P.n_cls * 2; q += TLANES)
+            dst[q] = src[q];
+        const int4 *src2 = reinterpret_cast<const int4 *>(g_ent);
+        int4 *dst2 = reinterpret_cast<int4 *>(s_ent);
+        for (int q = tid; q < n_ent * 2; q += TLANES)
+            dst2[q] = src2[q];
+        const int4 *src3 = reinterpret_cast<const int4 *>(g_spl);
+        int4 *dst3 = reinterpret_cast<int4 *>(s_spl);
+        for (int q = tid; q < n_spl; q += TLANES)
+            dst3[q] = src3[q];
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    unsigned char *wbase = smem_raw + L.warp + warp * L.warp_bytes;
+    int *w_cnt = reinterpret_cast<int *>(wbase);
+    unsigned *w_list = reinterpret_cast<unsigned *>(wbase + L.w_list);
+    float *w_best = reinterpret_cast<float *>(wbase + L.w_best);
+    __syncthreads();
+
+    const int n_jg = (P.n_xi + R - 1) / R;
+    const int n_flat = n_jg * P.n_t;
+    const int chunk0 = chunk * TLANES + warp * 32;  // first flat index of this warp
+    const int f_raw = chunk0 + lane;
+    const bool f_ok = f_raw < n_flat;
+    const int f = f_ok ? f_raw : n_flat - 1;
+    const int jg = f / P.n_t;
+    const int l = f - jg * P.n_t;
+    const int jb = jg * R;
+    const float one_m_gamma = __fsub_rn(1.f, P.gamma);
+    const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
+    const StageInfo si = stage_info(tb, k, v);
+    const float tl = node_val(P.t_lo, P.t_span, l, P.n_t);
+    const float wait = wait_time(tb, k, tl, si.wait_row);
+
+    int roff[R + 4];
+#pragma unroll
+    for (int w = 0; w < R + 4; ++w)
+        roff[w] = row_offset(P, jb - 2 + w);
+
+    // per row: the running minimum and the first class (in class order)
+    // reaching it; `tie` marks rows whose minimum a later class matches
+    // exactly (counted only: the order (value, class, control) decides)
+    float best[R];
+    int bcls[R];
+    unsigned tie = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        best[r] = __int_as_float(0x7f800000);
+        bcls[r] = 0;
+    }
+    for (int e = 0; e < n_ent; ++e) {
+        const ClassEntry E = s_ent[e];
+        const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
+        float G[R + 4];
+#pragma unroll
+        for (int w = 0; w < R + 4; ++w) {
+            const float g = blend<NC>(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
+            G[w] = x.red ? V_BIG : g;
+        }
+        float2 EV[R / 2 + 2], OD[R / 2 + 1];
+#pragma unroll
+        for (int p = 0; p < R / 2 + 2; ++p)
+            EV[p] = make_float2(G[2 * p], G[2 * p + 1]);
+#pragma unroll
+        for (int p = 0; p < R / 2 + 1; ++p)
+            OD[p] = make_float2(G[2 * p + 1], G[2 * p + 2]);
+        float cm[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            cm[r] = __int_as_float(0x7f800000);
+        int q = E.off;
+        bucket_min<R, -2>(s_spl, q, E.nb[0], EV, OD, cm);
+        q += E.nb[0];
+        bucket_min<R, -1>(s_spl, q, E.nb[1], EV, OD, cm);
+        q += E.nb[1];
+        bucket_min<R, 0>(s_spl, q, E.nb[2], EV, OD, cm);
+        q += E.nb[2];
+        bucket_min<R, 1>(s_spl, q, E.nb[3], EV, OD, cm);
+        q += E.nb[3];
+        for (int n = 0; n < E.n_other; ++n, ++q) {
+            const SplitRec S = s_spl[q];
+            const int d = split_d(S);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                cm[r] = fminf(cm[r],
+                              split_value(S, g_at<NC>(P, x, jb + r + d), g_at<NC>(P, x, jb + r + d + 1)));
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (cm[r] < best[r]) {
+                best[r] = cm[r];
+                bcls[r] = e;
+                tie &= ~(1u << r);
+            } else if (cm[r] == best[r]) {
+                tie |= 1u << r;
+            }
+        }
+    }
+
+    // values now; argmin recovery below
+    unsigned todo = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = jb + r;
+        const bool valid = f_ok && j < P.n_xi;
+        const bool feas = valid && best[r] < V_FEAS_MAX;
+        if (feas)
+            todo |= 1u << r;
+        if (valid) {
+            Vk[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] =
+                feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
+            if (!feas)
+                pik[((size_t)i * P.n_xi + j) * P.n_t + l] = -1;
+        }
+    }
+    tie &= todo;
+    if (stats) {
+        const unsigned n_tie = __reduce_add_sync(FULL, (unsigned)__popc(tie));
+        const unsigned n_find = __reduce_add_sync(FULL, (unsigned)__popc(todo));
+        if (lane == 0) {
+            atomicAdd(stats + 2, (unsigned long long)n_tie);
+            atomicAdd(stats + 3, (unsigned long long)n_find);
+        }
+    }
+
+    // bucket the feasible states by their first winning class and recover the
+    // lowest winning control of that class, warp-wide class by class
+    for (int q = lane; q < n_ent; q += 32)
+        w_cnt[q] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if ((todo >> r) & 1u) {
+            atomicAdd(&w_cnt[bcls[r]], 1);
+            w_best[lane * R + r] = best[r];
+        }
+    }
+    __syncwarp();
+    int total = 0;  // exclusive scan of the counters, in place
+    for (int b0 = 0; b0 < n_ent; b0 += 32) {
+        const int q = b0 + lane;
+        const int x = q < n_ent ? w_cnt[q] : 0;
+        int incl = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d)
+                incl += y;
+        }
+        if (q < n_ent)
+            w_cnt[q] = total + incl - x;
+        total += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if ((todo >> r) & 1u) {
+            const int key = bcls[r];
+            const int pos = atomicAdd(&w_cnt[key], 1);
+            w_list[pos] = ((unsigned)key << 16) | (unsigned)(lane * R + r);
+        }
+    }
+    __syncwarp();
+    for (int q = lane; q < total; q += 32) {
+        const unsigned en = w_list[q];
+        const int e = (int)(en >> 16);
+        const int s = (int)(en & 0xffffu);
+        const int ln = s / R, r = s - ln * R;
+        const int fq = chunk0 + ln;
+        const int jgq = fq / P.n_t;
+        const int lq = fq - jgq * P.n_t;
+        const float tlq = node_val(P.t_lo, P.t_span, lq, P.n_t);
+        const float wq = wait_time(tb, k, tlq, si.wait_row);
+        const ClassEntry E = s_ent[e];
+        const TCtx x = class_ctx(P, Vn, s_cls[E.cls], lq, tlq, wq, si);
+        const int j = jgq * R + r;
+        pik[((size_t)i * P.n_xi + j) * P.n_t + lq] = (int16_t)class_lowest_u<NC>(P, x, E, s_spl, j, w_best[s]);
+    }
+}
+
+}  // namespace tile
+}  // namespace ecodp

@@ -232,6 +232,19 @@ struct StageScratch {
     unsigned long long *stats;
 };
 
+// One instance of a batch (device-resident descriptor).
+struct BatchInst {
+    StageTables tb;
+    StageScratch sc;
+    float *V;              // [N+1] padded stages
+    int16_t *pi;           // [N] stages
+    size_t stage_elems, pi_elems;
+    int N, chunks, tiles;  // lane chunks per speed row and tiles per stage of the batched kernel
+    int pad;
+    int *done;             // [N] completed tiles of each stage (stage k at done[k])
+    long long row_off;     // first block of this instance in the batched precompute grid
+};
+
 // Limits of the tiled path (validated at create): controls per problem and
 // torque classes (per-control and per-class tables live in shared memory).
 constexpr int MAX_CONTROLS = 8192;
@@ -249,5 +262,36 @@ cudaError_t launch_dense_from_pad(const DevParams &hP, const float *padded, floa
 cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
                            size_t stage_elems, double v0, double xi0, double t0, double *out, int *out_u,
                            cudaStream_t s);
+
+// ---- batched instances (device descriptors in params[b], inst[b]) ----------
+
+// Work list of the persistent Bellman launch (device arrays).
+struct BatchSched {
+    const int *order;        // [B] instances by decreasing horizon (ties: index)
+    const long long *pref;   // [B + 1] prefix sums over `order` of tiles per stage
+    const long long *start;  // [max_n + 1] first item of each wavefront step
+    const int *m;            // [max_n] instances taking part in each step
+    int max_n;
+    long long n_items;
+    unsigned long long *queue;  // next item (zero before the launch)
+    int *error;                 // set to 1 when a dependency wait times out
+};
+
+cudaError_t launch_terminal_batched(const DevParams *params, const BatchInst *inst, int n_inst, cudaStream_t s);
+// Tables of every stage of every instance: n_rows = sum over b of N_b n_v_b.
+cudaError_t launch_precompute_batched(const DevParams *params, const BatchInst *inst, int n_inst, long long n_rows,
+                                      int max_n_u, cudaStream_t s);
+// The persistent Bellman launch; rows_per_lane in {4, 8}; ctas_per_sm <= 0:
+// as many as fit.
+cudaError_t launch_persistent(const DevParams *params, const BatchInst *inst, const BatchSched &S, int rows_per_lane,
+                              int max_n_cls, int max_n_u, int ctas_per_sm, cudaStream_t s);
+size_t persistent_smem_bytes(int rows_per_lane, int max_n_cls, int max_n_u);
+int persistent_chunks_per_row(int rows_per_lane, int n_xi, int n_t);
+int persistent_max_ctas_per_sm(int rows_per_lane, int max_n_cls, int max_n_u);
+// One CTA per instance; instance b writes [3(N+1) + 3N + 4] doubles at
+// out + out_off[b] and N ints at out_u + u_off[b] (layout of launch_rollout).
+cudaError_t launch_rollout_batched(const DevParams *params, const BatchInst *inst, int n_inst, const double *x0,
+                                   const long long *out_off, const long long *u_off, double *out, int *out_u,
+                                   cudaStream_t s);
 
 }  // namespace ecodp

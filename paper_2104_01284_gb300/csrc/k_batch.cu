@@ -1,0 +1,184 @@
+// Batched backward sweeps of many uneven instances in one persistent launch.
+//
+// Work items are (instance b, stage k, tile) with the tiles of bellman_tile.
+// They are handed out from a device counter in wavefront order: every
+// instance's first backward stage (k = N_b - 1), then every instance's second,
+// and so on; within a step the instances follow in order of decreasing
+// horizon, so the instances taking part in step j are a prefix of that order.
+// A tile of stage k needs all tiles of stage k + 1 of the same instance; it
+// waits on that stage's completion counter (acquire), bounded by a time limit
+// after which it records an error and goes on.  Items are only handed to
+// CTAs that are running (they fetch them), and every wait is for items handed
+// out earlier: the unfinished item fetched first has all its inputs, so the
+// waits cannot deadlock whatever the number of resident CTAs.
+#include "bellman_tile.cuh"
+
+namespace ecodp {
+
+namespace {
+
+using namespace tile;
+
+constexpr unsigned long long WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;  // 10 s
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(int *p, int v)
+{
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ int upper_bound_idx(const T *a, int n, T x)  // first index with a[idx] > x
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (a[mid] <= x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <int R>
+__global__ void __launch_bounds__(TLANES, 4) bellman_persistent(const DevParams *__restrict__ params,
+                                                               const BatchInst *__restrict__ inst, BatchSched S)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ DevParams P;
+    __shared__ long long s_item;
+    __shared__ int s_b, s_tile, s_j;
+    int cur_b = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long item = (long long)atomicAdd(S.queue, 1ull);
+            s_item = item;
+            if (item < S.n_items) {
+                const int j = upper_bound_idx(S.start, S.max_n + 1, item) - 1;
+                const long long r = item - S.start[j];
+                const int rank = upper_bound_idx(S.pref, S.m[j] + 1, r) - 1;
+                s_j = j;
+                s_b = S.order[rank];
+                s_tile = (int)(r - S.pref[rank]);
+            }
+        }
+        __syncthreads();
+        if (s_item >= S.n_items)
+            break;
+        const int b = s_b;
+        if (b != cur_b) {
+            __syncthreads();  // P is still read by the previous tile until here
+            if (threadIdx.x == 0)
+                P = params[b];
+            __syncthreads();
+            cur_b = b;
+        }
+        const BatchInst &I = inst[b];
+        const int k = I.N - 1 - s_j;
+        const int i = s_tile / I.chunks;
+        const int chunk = s_tile - i * I.chunks;
+        if (k + 1 < I.N) {  // stage k + 1 must be complete (stage N is the terminal cost)
+            if (threadIdx.x == 0) {
+                const unsigned long long t0 = global_ns();
+                while (ld_acquire(I.done + k + 1) < I.tiles) {
+                    if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                        atomicExch(S.error, 1);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            __syncthreads();
+            (void)ld_acquire(I.done + k + 1);  // every thread orders its reads after the writers
+        }
+        const size_t row = (size_t)k * P.n_v + i;
+        bellman_tile<R, false>(P, I.tb, k, I.sc.cls + row * P.n_cls, I.sc.ent + row * P.n_cls,
+                               I.sc.spl + row * P.n_u, I.sc.row_cnt[2 * row], I.sc.row_cnt[2 * row + 1],
+                               I.V + (size_t)(k + 1) * I.stage_elems, I.V + (size_t)k * I.stage_elems,
+                               I.pi + (size_t)k * I.pi_elems, i, chunk, smem_raw, nullptr);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            red_release_add(I.done + k, 1);
+        }
+    }
+}
+
+template <int R>
+cudaError_t max_ctas_r(size_t smem, int *per_sm)
+{
+    cudaError_t err =
+        cudaFuncSetAttribute(bellman_persistent<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return err;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bellman_persistent<R>, TLANES, smem);
+    if (err != cudaSuccess)
+        return err;
+    return *per_sm < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
+
+template <int R>
+cudaError_t launch_persistent_r(const DevParams *params, const BatchInst *inst, const BatchSched &S, size_t smem,
+                                int ctas_per_sm, int num_sms, cudaStream_t s)
+{
+    int per_sm = 0;
+    cudaError_t err = max_ctas_r<R>(smem, &per_sm);
+    if (err != cudaSuccess)
+        return err;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm)
+        per_sm = ctas_per_sm;
+    bellman_persistent<R><<<num_sms * per_sm, TLANES, smem, s>>>(params, inst, S);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t persistent_smem_bytes(int rows_per_lane, int max_n_cls, int max_n_u)
+{
+    return rows_per_lane == 4 ? layout<4>(max_n_cls, max_n_u).total : layout<8>(max_n_cls, max_n_u).total;
+}
+
+int persistent_chunks_per_row(int rows_per_lane, int n_xi, int n_t)
+{
+    return rows_per_lane == 4 ? chunks_per_row<4>(n_xi, n_t) : chunks_per_row<8>(n_xi, n_t);
+}
+
+int persistent_max_ctas_per_sm(int rows_per_lane, int max_n_cls, int max_n_u)
+{
+    const size_t smem = persistent_smem_bytes(rows_per_lane, max_n_cls, max_n_u);
+    int per_sm = 0;
+    const cudaError_t err = rows_per_lane == 4 ? max_ctas_r<4>(smem, &per_sm) : max_ctas_r<8>(smem, &per_sm);
+    return err == cudaSuccess ? per_sm : 0;
+}
+
+cudaError_t launch_persistent(const DevParams *params, const BatchInst *inst, const BatchSched &S, int rows_per_lane,
+                              int max_n_cls, int max_n_u, int ctas_per_sm, cudaStream_t s)
+{
+    int dev = 0, num_sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess)
+        return err;
+    err = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess)
+        return err;
+    const size_t smem = persistent_smem_bytes(rows_per_lane, max_n_cls, max_n_u);
+    if (rows_per_lane == 4)
+        return launch_persistent_r<4>(params, inst, S, smem, ctas_per_sm, num_sms, s);
+    return launch_persistent_r<8>(params, inst, S, smem, ctas_per_sm, num_sms, s);
+}
+
+}  // namespace ecodp

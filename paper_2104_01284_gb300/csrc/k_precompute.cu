@@ -119,19 +119,10 @@ struct CtrlRec {
     int d, ok;
 };
 
-__global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
-                                                         int k_first, StageScratch sc)
+// Tables of speed row i of stage k (one CTA of 256 threads; P in shared memory).
+__device__ void precompute_row(const DevParams &P, const StageTables &tb, int k, int i, const StageScratch &sc,
+                               CtrlRec *s_ctrl, int *scan_buf)
 {
-    extern __shared__ __align__(16) unsigned char pre_smem[];
-    CtrlRec *s_ctrl = reinterpret_cast<CtrlRec *>(pre_smem);
-    __shared__ DevParams P;
-    __shared__ int scan_buf[256];
-    if (threadIdx.x == 0)
-        P = *dP;
-    __syncthreads();
-
-    const int i = blockIdx.x;
-    const int k = k_first + blockIdx.y;
     const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
     const float p = tb.grade[k];
     const float sq = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(p, p)));
@@ -263,7 +254,86 @@ __global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__rest
     }
 }
 
+__global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
+                                                         int k_first, StageScratch sc)
+{
+    extern __shared__ __align__(16) unsigned char pre_smem[];
+    __shared__ DevParams P;
+    __shared__ int scan_buf[256];
+    if (threadIdx.x == 0)
+        P = *dP;
+    __syncthreads();
+    precompute_row(P, tb, k_first + blockIdx.y, blockIdx.x, sc, reinterpret_cast<CtrlRec *>(pre_smem), scan_buf);
+}
+
+// Batched: one CTA per (instance, stage, speed row); blocks of instance b
+// start at inst[b].row_off (rows of all its stages, stage-major).
+__global__ void __launch_bounds__(256) precompute_batched_kernel(const DevParams *__restrict__ params,
+                                                                 const BatchInst *__restrict__ inst, int n_inst)
+{
+    extern __shared__ __align__(16) unsigned char pre_smem[];
+    __shared__ DevParams P;
+    __shared__ int scan_buf[256];
+    __shared__ int s_b;
+    const long long blk = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_inst - 1;  // last instance with row_off <= blk
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (inst[mid].row_off <= blk)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_b = lo;
+        P = params[lo];
+    }
+    __syncthreads();
+    const BatchInst &I = inst[s_b];
+    const long long r = blk - I.row_off;
+    precompute_row(P, I.tb, (int)(r / P.n_v), (int)(r % P.n_v), I.sc, reinterpret_cast<CtrlRec *>(pre_smem),
+                   scan_buf);
+}
+
+// Batched terminal values J_N = c_T for every instance (grid-stride over instances' states).
+__global__ void terminal_batched_kernel(const DevParams *__restrict__ params, const BatchInst *__restrict__ inst,
+                                        int n_inst)
+{
+    const int b = blockIdx.y;
+    if (b >= n_inst)
+        return;
+    const DevParams &P = params[b];
+    const BatchInst &I = inst[b];
+    float *VN = I.V + (size_t)P.N * I.stage_elems;
+    const int total = P.n_v * P.n_xi * P.n_t;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+        const int l = s % P.n_t;
+        const int j = (s / P.n_t) % P.n_xi;
+        const int i = s / (P.n_t * P.n_xi);
+        VN[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] =
+            terminal_cost(P, node_val(P.v_lo, P.v_span, i, P.n_v), node_val(P.xi_lo, P.xi_span, j, P.n_xi));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_precompute_batched(const DevParams *params, const BatchInst *inst, int n_inst, long long n_rows,
+                                      int max_n_u, cudaStream_t s)
+{
+    const size_t smem = (size_t)max_n_u * sizeof(CtrlRec);
+    cudaError_t err =
+        cudaFuncSetAttribute(precompute_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return err;
+    precompute_batched_kernel<<<(unsigned)n_rows, 256, smem, s>>>(params, inst, n_inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_terminal_batched(const DevParams *params, const BatchInst *inst, int n_inst, cudaStream_t s)
+{
+    terminal_batched_kernel<<<dim3(64, n_inst), 256, 0, s>>>(params, inst, n_inst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fill(float *p, size_t n, float val, cudaStream_t s)
 {

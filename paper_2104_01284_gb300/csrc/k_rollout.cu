@@ -101,10 +101,10 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
 
 constexpr int ROLL_THREADS = 512;
 
-__global__ void __launch_bounds__(ROLL_THREADS) rollout_kernel(const DevParams *__restrict__ dP, StageTables tb,
-                                                               const float *__restrict__ Vall, size_t stage_elems,
-                                                               double v0, double xi0, double t0,
-                                                               double *__restrict__ out, int *__restrict__ out_u)
+// The rollout of one problem by the whole CTA.
+__device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables &tb, const float *__restrict__ Vall,
+                             size_t stage_elems, double v0, double xi0, double t0, double *__restrict__ out,
+                             int *__restrict__ out_u)
 {
     __shared__ DevParams P;
     __shared__ float s_v, s_xi;
@@ -204,6 +204,27 @@ __global__ void __launch_bounds__(ROLL_THREADS) rollout_kernel(const DevParams *
     }
 }
 
+__global__ void __launch_bounds__(ROLL_THREADS) rollout_kernel(const DevParams *__restrict__ dP, StageTables tb,
+                                                               const float *__restrict__ Vall, size_t stage_elems,
+                                                               double v0, double xi0, double t0,
+                                                               double *__restrict__ out, int *__restrict__ out_u)
+{
+    rollout_body(dP, tb, Vall, stage_elems, v0, xi0, t0, out, out_u);
+}
+
+// Batched: one CTA per instance; instance b writes its output block at
+// out + out_off[b] (doubles) and out_u + u_off[b].
+__global__ void __launch_bounds__(ROLL_THREADS)
+    rollout_batched_kernel(const DevParams *__restrict__ params, const BatchInst *__restrict__ inst,
+                           const double *__restrict__ x0, const long long *__restrict__ out_off,
+                           const long long *__restrict__ u_off, double *__restrict__ out, int *__restrict__ out_u)
+{
+    const int b = blockIdx.x;
+    const BatchInst &I = inst[b];
+    rollout_body(params + b, I.tb, I.V, I.stage_elems, x0[3 * b], x0[3 * b + 1], x0[3 * b + 2], out + out_off[b],
+                 out_u + u_off[b]);
+}
+
 }  // namespace
 
 cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
@@ -212,6 +233,14 @@ cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables
 {
     (void)hP;
     rollout_kernel<<<1, ROLL_THREADS, 0, s>>>(dP, tb, Vall, stage_elems, v0, xi0, t0, out, out_u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_batched(const DevParams *params, const BatchInst *inst, int n_inst, const double *x0,
+                                   const long long *out_off, const long long *u_off, double *out, int *out_u,
+                                   cudaStream_t s)
+{
+    rollout_batched_kernel<<<n_inst, ROLL_THREADS, 0, s>>>(params, inst, x0, out_off, u_off, out, out_u);
     return cudaGetLastError();
 }
 

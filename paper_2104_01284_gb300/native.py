@@ -111,3 +111,26 @@ EXPORTED.append("dp_solve_stage_static")
 # adjoint dJ_0(x0)/dtheta, theta = (mass, CdA, Crr, R0, fuel_scale)
 dp_adjoint = _sig("dp_adjoint", vp, dbl_p, dbl_p, dbl_p, vp)
 EXPORTED.append("dp_adjoint")
+
+# batches of independent problems (one persistent Bellman launch)
+
+
+class MultiOpts(C.Structure):
+    _fields_ = [("rows_per_lane", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+dp_multi_create = _sig("dp_multi_create", C.POINTER(ProblemDesc), C.c_int32, C.POINTER(MultiOpts),
+                       C.POINTER(Allocator), vp, C.POINTER(vp))
+dp_multi_destroy = _sig("dp_multi_destroy", vp)
+dp_multi_set_config = _sig("dp_multi_set_config", vp, C.c_int32, C.c_int32)
+dp_multi_solve = _sig("dp_multi_solve", vp, vp)
+dp_multi_wait = _sig("dp_multi_wait", vp, vp)
+dp_multi_profile = _sig("dp_multi_profile", vp, vp, C.POINTER(C.c_float))
+dp_multi_autotune = _sig("dp_multi_autotune", vp, vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float))
+dp_multi_info = _sig("dp_multi_info", vp, C.POINTER(C.c_int64))
+dp_multi_get_value = _sig("dp_multi_get_value", vp, C.c_int32, C.c_int32, vp, C.c_int32, vp)
+dp_multi_get_policy = _sig("dp_multi_get_policy", vp, C.c_int32, C.c_int32, vp, C.c_int32, vp)
+dp_multi_rollout = _sig("dp_multi_rollout", vp, dbl_p, C.POINTER(Trajectory), vp)
+EXPORTED += ["dp_multi_create", "dp_multi_destroy", "dp_multi_set_config", "dp_multi_solve", "dp_multi_wait",
+             "dp_multi_profile", "dp_multi_autotune", "dp_multi_info", "dp_multi_get_value", "dp_multi_get_policy",
+             "dp_multi_rollout"]

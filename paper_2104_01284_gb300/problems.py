@@ -38,6 +38,7 @@ __all__ = [
     "config1",
     "config2_seeds",
     "config3_batch",
+    "config3_small",
     "config4_fleet",
     "toy_problem",
     "uniform_nodes",
@@ -270,6 +271,40 @@ def config3_batch(seed: int = 3, n_instances: int = 256) -> list[Problem]:
             t_lo=0.0, t_hi=2.0 * n_stages, n_t=n_t,
             te_lo=0.0, te_hi=200.0, n_te=n_u, tm_lo=-100.0, tm_hi=100.0, n_tm=n_u,
             n_brake=2, fuel_coef=fuel, light_stage=nodes, cycle=cyc, red=red, offset=off))
+    return out
+
+
+def config3_small(seed: int = 33, n_instances: int = 6) -> list[Problem]:
+    """Uneven instances at sizes the oracle sweeps in seconds, for batch
+    parity: per instance, in order, horizon U{4..14} stages, n_v U{9..21},
+    n_soc U{7..19}, n_t U{17..45}, n_te U{5..9}, n_tm U{5..9} (unequal steps
+    give one torque class per control), brake flag with probability 1/2,
+    lights U{1..3} with short cycles U(6, 14) s (red fraction 0.3-0.6), then
+    the fuel map and grade.  t spans 2.5 s per step."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for b in range(n_instances):
+        n_stages = int(rng.integers(4, 15))
+        n_v = int(rng.integers(9, 22))
+        n_soc = int(rng.integers(7, 20))
+        n_t = int(rng.integers(17, 46))
+        n_te = int(rng.integers(5, 10))
+        n_tm = int(rng.integers(5, 10))
+        n_brake = int(rng.integers(1, 3))
+        n_l = min(int(rng.integers(1, 4)), n_stages - 1)
+        fuel = _draw_fuel(rng)
+        grade = rng.uniform(-0.03, 0.03, size=n_stages)
+        nodes = np.sort(rng.choice(np.arange(1, n_stages), size=n_l, replace=False)).astype(np.int32)
+        cyc = rng.uniform(6.0, 14.0, n_l)
+        red = cyc * rng.uniform(0.3, 0.6, n_l)
+        off = rng.uniform(0.0, 1.0, n_l) * cyc
+        out.append(Problem(
+            name=f"c3-small-s{seed}-{b}", n_stages=n_stages, ds=10.0, grade=grade,
+            v_lo=0.0, v_hi=20.0, n_v=n_v, soc_lo=0.40, soc_hi=0.70, n_soc=n_soc,
+            t_lo=0.0, t_hi=2.5 * n_stages, n_t=n_t,
+            te_lo=0.0, te_hi=200.0, n_te=n_te, tm_lo=-100.0, tm_hi=100.0, n_tm=n_tm,
+            n_brake=n_brake, fuel_coef=fuel, light_stage=nodes, cycle=cyc, red=red, offset=off,
+            x0=(4.0, 0.58, 0.0)))
     return out
 
 

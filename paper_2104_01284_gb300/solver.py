@@ -244,3 +244,145 @@ class EcoDPValue(torch.autograd.Function):
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
         return grad_out * g, None, None, None
+
+
+def _trajectory_buffers(n):
+    bufs = dict(v=np.empty(n + 1), soc=np.empty(n + 1), t=np.empty(n + 1), u=np.empty(n, np.int32),
+                dt=np.empty(n), wait=np.empty(n), fuel=np.empty(n))
+    tr = N.Trajectory()
+    for key, a in bufs.items():
+        ct = C.c_int32 if a.dtype == np.int32 else C.c_double
+        setattr(tr, key, a.ctypes.data_as(C.POINTER(ct)))
+    return bufs, tr
+
+
+class EcoDPBatch:
+    """Many independent problems (any horizons, grids and controls) solved by
+    one persistent Bellman launch under a CUDA graph.  Values and policies are
+    bit-identical to EcoDP's on the same problem.
+
+    >>> batch = EcoDPBatch(problems.config3_batch())
+    >>> batch.autotune()          # pick rows_per_lane / CTAs per SM
+    >>> batch.solve()
+    >>> trajs = batch.rollout()
+    """
+
+    def __init__(self, probs, device=None, stream=None, rows_per_lane: int = 0, ctas_per_sm: int = 0,
+                 use_torch_allocator: bool = True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("EcoDPBatch needs a CUDA device; the solver has no CPU fallback")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.probs = list(probs)
+        self._alloc = TorchAllocator(self.device) if use_torch_allocator else None
+        descs = (N.ProblemDesc * len(self.probs))()
+        keep = []
+        for b, p in enumerate(self.probs):
+            d, k = make_desc(p)
+            descs[b] = d
+            keep.append(k)
+        opts = N.MultiOpts(int(rows_per_lane), int(ctas_per_sm))
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_create(descs, len(self.probs), C.byref(opts),
+                                      C.byref(self._alloc.struct) if self._alloc else None, _stream_handle(stream),
+                                      C.byref(h)), "dp_multi_create")
+        del keep
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            with torch.cuda.device(self.device):
+                N.check(N.dp_multi_destroy(self.h), "dp_multi_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.probs)
+
+    def set_config(self, rows_per_lane: int, ctas_per_sm: int):
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_set_config(self.h, int(rows_per_lane), int(ctas_per_sm)), "dp_multi_set_config")
+
+    def solve(self, stream=None):
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_solve(self.h, _stream_handle(stream)), "dp_multi_solve")
+
+    def wait(self, stream=None):
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_wait(self.h, _stream_handle(stream)), "dp_multi_wait")
+
+    def profile(self, stream=None):
+        ms = (C.c_float * 3)()
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_profile(self.h, _stream_handle(stream), ms), "dp_multi_profile")
+        return dict(precompute=ms[0], bellman=ms[1], solve=ms[2])
+
+    def autotune(self, repeats: int = 1, stream=None):
+        best = (C.c_int32 * 2)()
+        t = C.c_float(0.0)
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_autotune(self.h, _stream_handle(stream), int(repeats), best, C.byref(t)),
+                    "dp_multi_autotune")
+        return dict(rows_per_lane=best[0], ctas_per_sm=best[1], ms=t.value)
+
+    def info(self):
+        out = (C.c_int64 * 8)()
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_info(self.h, out), "dp_multi_info")
+        keys = ("instances", "work_items", "ctas", "rows_per_lane", "ctas_per_sm", "nominal_evals", "device_bytes",
+                "max_horizon")
+        return dict(zip(keys, list(out)))
+
+    def _shape(self, b):
+        if not 0 <= b < len(self.probs):
+            return (1,)  # the library rejects the index
+        p = self.probs[b]
+        return (p.n_v, p.n_soc, p.n_t)
+
+    def value(self, b: int, k: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self._shape(b), dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_get_value(self.h, int(b), int(k), out.data_ptr(), 0, _stream_handle(stream)),
+                    "dp_multi_get_value")
+        return out
+
+    def policy(self, b: int, k: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self._shape(b), dtype=torch.int16, device=self.device)
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_get_policy(self.h, int(b), int(k), out.data_ptr(), 0, _stream_handle(stream)),
+                    "dp_multi_get_policy")
+        return out
+
+    def rollout(self, x0=None, stream=None, raise_infeasible: bool = True):
+        """Rollout of every instance from x0 ([n, 3]; default each problem's
+        x0); returns a list of dicts like EcoDP.rollout."""
+        B = len(self.probs)
+        x = np.array([p.x0 for p in self.probs] if x0 is None else x0, dtype=np.float64).reshape(B, 3)
+        trs = (N.Trajectory * B)()
+        bufs = []
+        for b, p in enumerate(self.probs):
+            bb, tr = _trajectory_buffers(p.n_stages)
+            trs[b] = tr
+            bufs.append(bb)
+        with torch.cuda.device(self.device):
+            st = N.dp_multi_rollout(self.h, x.ctypes.data_as(C.POINTER(C.c_double)), trs, _stream_handle(stream))
+        if st != N.DP_OK and (raise_infeasible or st != N.DP_ERR_INFEASIBLE):
+            N.check(st, "dp_multi_rollout")
+        outs = []
+        for b in range(B):
+            o = dict(bufs[b])
+            o["traj"] = np.stack([o["v"], o["soc"], o["t"]], axis=1)
+            o.update(fuel_g=trs[b].fuel_g, time_s=trs[b].time_s, J=trs[b].J, fail_stage=trs[b].fail_stage)
+            outs.append(o)
+        return outs

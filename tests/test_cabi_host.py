@@ -87,3 +87,20 @@ def test_product_code_never_uses_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "ecodp_oracle" not in src, f
+
+
+def test_multi_create_rejects_bad_instance(native):
+    from paper_2104_01284_gb300.solver import make_desc
+    probs = P.config3_small(seed=35, n_instances=3)
+    probs[2] = probs[2].replace(n_soc=1)
+    descs = (native.ProblemDesc * 3)()
+    keep = []
+    for b, p in enumerate(probs):
+        d, k = make_desc(p)
+        descs[b] = d
+        keep.append(k)
+    h = C.c_void_p()
+    st = native.dp_multi_create(descs, 3, None, None, None, C.byref(h))
+    assert st == native.DP_ERR_INVALID_ARG and h.value is None
+    assert b"instance 2" in native.lib.dp_last_error()
+    assert native.dp_multi_create(descs, 0, None, None, None, C.byref(h)) == native.DP_ERR_INVALID_ARG
