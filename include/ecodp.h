@@ -117,9 +117,11 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
                             dp_problem_t *out);
 
 /* Replace the problem's route data and parameters (grade, lights, model
- * constants; Eq. 5-8) with those of desc, which must have the same sizes
- * (stages, grids, controls) and light count; asynchronous on stream.
- * Previously computed results become stale (DP_ERR_NOT_SOLVED). */
+ * constants, grid ranges; Eq. 5-8) with those of desc, which must have the
+ * same sizes (stages, grid points, controls, torque classes); the number of
+ * lights may change.  Asynchronous on stream (the host tables are copied
+ * before the call returns).  Previously computed results become stale
+ * (DP_ERR_NOT_SOLVED). */
 dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *stream);
 
 /* Free everything (through the caller's allocator). NULL is accepted. */
@@ -310,6 +312,52 @@ dp_status dp_multi_get_policy(dp_multi_t m, int32_t b, int32_t stage, int16_t *o
  * if any instance has a stage without a feasible control (every
  * trajectory's fail_stage tells which). */
 dp_status dp_multi_rollout(dp_multi_t m, const double *x0, dp_trajectory *traj, void *stream);
+
+/* ---- Serving: continuous batching of receding-horizon re-solves ---------
+ *
+ * The paper's controller re-solves the look-ahead problem as the vehicle
+ * advances (receding horizon, Sec. III); a server re-solves for many
+ * vehicles at once.  A dp_batch holds up to max_slots slots; each is a
+ * resident problem with its own CUDA stream, so requests submitted while
+ * others are on the GPU run concurrently with them.  A request's result is
+ * identical to dp_solve_backward + dp_rollout of the same descriptor alone
+ * (same kernels, same arithmetic, no cross-request state).
+ *
+ * Memory: a slot's device memory (value function, policy, tables) stays
+ * allocated after its request is collected; the next request whose sizes
+ * match re-uses it through an in-place table update (dp_problem_update).
+ * New slots are created only while the sum of the slots' device bytes stays
+ * within mem_budget.  Slots and results are owned by the batch; trajectories
+ * by the caller.  Calls on one batch are serialised by an internal lock. */
+typedef struct dp_batch *dp_batch_t;
+
+/* Errors: DP_ERR_INVALID_ARG (max_slots outside [1, 4096], mem_budget 0,
+ * allocator with a NULL function), DP_ERR_OOM. */
+dp_status dp_batch_create(int32_t max_slots, size_t mem_budget, const dp_allocator *alloc, dp_batch_t *out);
+
+/* Wait for every slot's work and free all device and pinned memory. NULL is
+ * accepted.  Uncollected results are discarded. */
+dp_status dp_batch_destroy(dp_batch_t b);
+
+/* Admit one request: the problem desc (validated as in dp_problem_create)
+ * and the rollout start x0 = {v, soc, t} (host).  Non-blocking: enqueues the
+ * backward sweep (Eq. 9), the forward rollout and the copy of its result on
+ * the slot's stream and returns a ticket.  DP_ERR_OOM when no slot is free
+ * and no new slot fits in the budget (the request is not admitted: collect
+ * finished requests with dp_batch_poll and submit again). */
+dp_status dp_batch_submit(dp_batch_t b, const dp_problem_desc *desc, const double x0[3], uint64_t *ticket);
+
+/* Collect a request: DP_ERR_NOT_SOLVED while it is still running (nothing
+ * written); otherwise fills the caller's trajectory (host arrays sized for
+ * the request's n_stages), frees the slot and returns DP_OK, or
+ * DP_ERR_INFEASIBLE when the rollout found a stage without a feasible
+ * control.  DP_ERR_INVALID_ARG for a ticket that is unknown or collected. */
+dp_status dp_batch_poll(dp_batch_t b, uint64_t ticket, dp_trajectory *traj);
+
+/* out[0] slots, out[1] busy slots, out[2] device bytes held, out[3]
+ * requests admitted, out[4] collected, out[5] submit attempts refused with DP_ERR_OOM,
+ * out[6] slot creations, out[7] admissions that re-used a slot's memory. */
+dp_status dp_batch_stats(dp_batch_t b, int64_t out[8]);
 
 #ifdef __cplusplus
 }

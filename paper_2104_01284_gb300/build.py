@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libecodp.so")
-SOURCES = ["api.cu", "api_multi.cu", "k_precompute.cu", "k_bellman.cu", "k_rollout.cu", "k_adjoint.cu", "k_batch.cu"]
+SOURCES = ["api.cu", "api_multi.cu", "api_serve.cu", "k_precompute.cu", "k_bellman.cu", "k_rollout.cu", "k_adjoint.cu", "k_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(os.path.dirname(HERE), "include")]

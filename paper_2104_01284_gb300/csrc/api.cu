@@ -1,6 +1,7 @@
 // C ABI of the ecodp solver (declared in include/ecodp.h): problem objects,
 // validation, device memory through the caller's allocator, the CUDA-graph
 // captured backward sweep, result copies and the rollout.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -45,6 +46,7 @@ struct dp_problem {
     bool has_alloc = false;
     cudaStream_t create_stream = nullptr;
     std::vector<void *> blocks;
+    size_t bytes_held = 0;
 
     DevParams *dP = nullptr;
     float *d_grade = nullptr;
@@ -252,6 +254,7 @@ dp_status dev_alloc(dp_problem *p, size_t bytes, void **out)
         }
     }
     p->blocks.push_back(ptr);
+    p->bytes_held += bytes;
     *out = ptr;
     return DP_OK;
 }
@@ -311,6 +314,62 @@ dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 }
 
 }  // namespace
+
+namespace ecodp {
+namespace host {
+
+size_t roll_doubles(int N) { return (size_t)(3 * (N + 1) + 3 * N + 4); }
+
+dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s)
+{
+    DP_CUDA(launch_rollout(p->dP, p->hP, p->tables(), p->d_V, p->stage_elems, x0[0], x0[1], x0[2], p->d_roll,
+                           p->d_roll_u, s));
+    DP_CUDA(cudaMemcpyAsync(h_out, p->d_roll, roll_doubles(p->N) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DP_CUDA(cudaMemcpyAsync(h_u, p->d_roll_u, (size_t)p->N * sizeof(int), cudaMemcpyDeviceToHost, s));
+    return DP_OK;
+}
+
+int unpack_rollout(int N, const double *h, const int *hu, dp_trajectory *traj)
+{
+    const double *tot = h + 3 * (N + 1) + 3 * N;
+    const int fail_stage = (int)tot[3];
+    const int reached = fail_stage >= 0 ? fail_stage : N;
+    for (int q = 0; q <= N; ++q) {
+        const bool ok = q <= reached;
+        traj->v[q] = ok ? h[3 * q] : NAN;
+        traj->soc[q] = ok ? h[3 * q + 1] : NAN;
+        traj->t[q] = ok ? h[3 * q + 2] : NAN;
+    }
+    for (int q = 0; q < N; ++q) {
+        const bool ok = q < reached;
+        traj->u[q] = ok ? hu[q] : -1;
+        traj->dt[q] = ok ? h[3 * (N + 1) + q] : NAN;
+        traj->wait[q] = ok ? h[3 * (N + 1) + N + q] : NAN;
+        traj->fuel[q] = ok ? h[3 * (N + 1) + 2 * N + q] : NAN;
+    }
+    traj->fuel_g = tot[0];
+    traj->time_s = tot[1];
+    traj->J = tot[2];
+    traj->fail_stage = fail_stage;
+    return fail_stage;
+}
+
+size_t problem_bytes(const dp_problem *p) { return p->bytes_held; }
+
+int problem_stages(const dp_problem *p) { return p->N; }
+
+bool problem_fits(const dp_problem *p, const dp_problem_desc *d)
+{
+    if (d->n_stages != p->N || d->n_v != p->n_v || d->n_soc != p->n_xi || d->n_t != p->n_t ||
+        d->n_te * d->n_tm * d->n_brake != p->n_u || d->n_te != p->hP.n_te || d->n_brake != p->hP.n_b)
+        return false;
+    DevParams P;
+    fill_params(d, P);
+    return P.n_cls == p->hP.n_cls;
+}
+
+}  // namespace host
+}  // namespace ecodp
 
 extern "C" {
 
@@ -375,9 +434,12 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, 1, &p->dP));
     TRY(dev_alloc_n(p, p->h.grade.size(), &p->d_grade));
     TRY(dev_alloc_n(p, p->h.lon.size(), &p->d_lon));
-    TRY(dev_alloc_n(p, p->h.cyc.size(), &p->d_cyc));
-    TRY(dev_alloc_n(p, p->h.red.size(), &p->d_red));
-    TRY(dev_alloc_n(p, p->h.off.size(), &p->d_off));
+    // light tables sized for the most lights a route of N stages can hold,
+    // so that dp_problem_update may change the light count
+    const size_t light_cap = std::max<size_t>(p->h.cyc.size(), (size_t)p->N);
+    TRY(dev_alloc_n(p, light_cap, &p->d_cyc));
+    TRY(dev_alloc_n(p, light_cap, &p->d_red));
+    TRY(dev_alloc_n(p, light_cap, &p->d_off));
     TRY(dev_alloc_n(p, p->stage_elems * (size_t)(p->N + 1), &p->d_V));
     TRY(dev_alloc_n(p, p->pi_elems * (size_t)p->N, &p->d_pi));
     if (P.n_cls > MAX_CLASSES) {
@@ -430,13 +492,14 @@ dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *s
         return st;
     if (desc->n_stages != p->N || desc->n_v != p->n_v || desc->n_soc != p->n_xi || desc->n_t != p->n_t ||
         desc->n_te * desc->n_tm * desc->n_brake != p->n_u || desc->n_te != p->hP.n_te ||
-        desc->n_brake != p->hP.n_b || desc->n_lights != p->n_lights)
-        return fail(DP_ERR_INVALID_ARG, "update must keep the problem's sizes and light count");
+        desc->n_brake != p->hP.n_b)
+        return fail(DP_ERR_INVALID_ARG, "update must keep the problem's sizes");
     DevParams P;
     fill_params(desc, P);
     if (P.n_cls != p->hP.n_cls)
         return fail(DP_ERR_INVALID_ARG, "update changes the torque class structure");
     p->hP = P;
+    p->n_lights = desc->n_lights;
     fill_tables(desc, p->h);
     st = upload_tables(p, (cudaStream_t)stream);
     p->solved = false;
@@ -679,33 +742,13 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
     cudaStream_t s = (cudaStream_t)stream;
     const int N = p->N;
-    DP_CUDA(launch_rollout(p->dP, p->hP, p->tables(), p->d_V, p->stage_elems, x0[0], x0[1], x0[2], p->d_roll,
-                           p->d_roll_u, s));
-    std::vector<double> h(3 * (N + 1) + 3 * N + 4);
+    std::vector<double> h(roll_doubles(N));
     std::vector<int> hu(N, -1);
-    DP_CUDA(cudaMemcpyAsync(h.data(), p->d_roll, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    DP_CUDA(cudaMemcpyAsync(hu.data(), p->d_roll_u, hu.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    dp_status st = rollout_async(p, x0, h.data(), hu.data(), s);
+    if (st != DP_OK)
+        return st;
     DP_CUDA(cudaStreamSynchronize(s));
-    const double *tot = h.data() + 3 * (N + 1) + 3 * N;
-    int fail_stage = (int)tot[3];
-    int reached = fail_stage >= 0 ? fail_stage : N;
-    for (int q = 0; q <= N; ++q) {
-        bool ok = q <= reached;
-        traj->v[q] = ok ? h[3 * q] : NAN;
-        traj->soc[q] = ok ? h[3 * q + 1] : NAN;
-        traj->t[q] = ok ? h[3 * q + 2] : NAN;
-    }
-    for (int q = 0; q < N; ++q) {
-        bool ok = q < reached;
-        traj->u[q] = ok ? hu[q] : -1;
-        traj->dt[q] = ok ? h[3 * (N + 1) + q] : NAN;
-        traj->wait[q] = ok ? h[3 * (N + 1) + N + q] : NAN;
-        traj->fuel[q] = ok ? h[3 * (N + 1) + 2 * N + q] : NAN;
-    }
-    traj->fuel_g = tot[0];
-    traj->time_s = tot[1];
-    traj->J = tot[2];
-    traj->fail_stage = fail_stage;
+    const int fail_stage = unpack_rollout(N, h.data(), hu.data(), traj);
     if (fail_stage >= 0)
         return fail(DP_ERR_INFEASIBLE, "no feasible control at stage " + std::to_string(fail_stage));
     return DP_OK;

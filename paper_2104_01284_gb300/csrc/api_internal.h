@@ -8,6 +8,8 @@
 #include "../../include/ecodp.h"
 #include "ecodp_internal.cuh"
 
+struct dp_problem;
+
 namespace ecodp {
 namespace host {
 
@@ -33,6 +35,18 @@ void fill_tables(const dp_problem_desc *d, HostTables &t);
 
 bool finite3(const double x[3]);
 const char *last_error();
+
+// Single-problem helpers (api.cu) for the batch and serving entry points.
+size_t roll_doubles(int N);  // doubles of one rollout record (launch_rollout's layout)
+// Launch the rollout of a solved problem and copy its record to host memory
+// (pinned for an asynchronous copy) on stream s; no synchronisation.
+dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s);
+// Fill a caller's trajectory from a rollout record; returns its fail stage.
+int unpack_rollout(int N, const double *h, const int *hu, dp_trajectory *traj);
+size_t problem_bytes(const dp_problem *p);  // device bytes the problem holds
+int problem_stages(const dp_problem *p);
+// Whether dp_problem_update can load d into p (same sizes and class structure).
+bool problem_fits(const dp_problem *p, const dp_problem_desc *d);
 
 }  // namespace host
 }  // namespace ecodp

@@ -110,8 +110,6 @@ void m_release(dp_multi *m)
     m->blocks.clear();
 }
 
-size_t roll_doubles(int N) { return (size_t)(3 * (N + 1) + 3 * N + 4); }
-
 // Tiles per stage for the current rows_per_lane, the wavefront work list and
 // the device descriptors (uploaded on stream s).
 dp_status build_schedule(dp_multi *m, cudaStream_t s)
@@ -563,31 +561,8 @@ dp_status dp_multi_rollout(dp_multi_t m, const double *x0, dp_trajectory *traj, 
         return st;
     int first_fail = -1;
     for (int b = 0; b < m->B; ++b) {
-        const int N = m->hP[b].N;
-        const double *o = h.data() + m->out_off[b];
-        const int *ou = hu.data() + m->u_off[b];
-        const double *tot = o + 3 * (N + 1) + 3 * N;
-        const int fail_stage = (int)tot[3];
-        const int reached = fail_stage >= 0 ? fail_stage : N;
-        dp_trajectory &T = traj[b];
-        for (int q = 0; q <= N; ++q) {
-            const bool ok = q <= reached;
-            T.v[q] = ok ? o[3 * q] : NAN;
-            T.soc[q] = ok ? o[3 * q + 1] : NAN;
-            T.t[q] = ok ? o[3 * q + 2] : NAN;
-        }
-        for (int q = 0; q < N; ++q) {
-            const bool ok = q < reached;
-            T.u[q] = ok ? ou[q] : -1;
-            T.dt[q] = ok ? o[3 * (N + 1) + q] : NAN;
-            T.wait[q] = ok ? o[3 * (N + 1) + N + q] : NAN;
-            T.fuel[q] = ok ? o[3 * (N + 1) + 2 * N + q] : NAN;
-        }
-        T.fuel_g = tot[0];
-        T.time_s = tot[1];
-        T.J = tot[2];
-        T.fail_stage = fail_stage;
-        if (fail_stage >= 0 && first_fail < 0)
+        const int fs = unpack_rollout(m->hP[b].N, h.data() + m->out_off[b], hu.data() + m->u_off[b], &traj[b]);
+        if (fs >= 0 && first_fail < 0)
             first_fail = b;
     }
     if (first_fail >= 0)

@@ -134,3 +134,11 @@ dp_multi_rollout = _sig("dp_multi_rollout", vp, dbl_p, C.POINTER(Trajectory), vp
 EXPORTED += ["dp_multi_create", "dp_multi_destroy", "dp_multi_set_config", "dp_multi_solve", "dp_multi_wait",
              "dp_multi_profile", "dp_multi_autotune", "dp_multi_info", "dp_multi_get_value", "dp_multi_get_policy",
              "dp_multi_rollout"]
+
+# serving: continuous batching of receding-horizon re-solves
+dp_batch_create = _sig("dp_batch_create", C.c_int32, C.c_size_t, C.POINTER(Allocator), C.POINTER(vp))
+dp_batch_destroy = _sig("dp_batch_destroy", vp)
+dp_batch_submit = _sig("dp_batch_submit", vp, C.POINTER(ProblemDesc), dbl_p, C.POINTER(C.c_uint64))
+dp_batch_poll = _sig("dp_batch_poll", vp, C.c_uint64, C.POINTER(Trajectory))
+dp_batch_stats = _sig("dp_batch_stats", vp, C.POINTER(C.c_int64))
+EXPORTED += ["dp_batch_create", "dp_batch_destroy", "dp_batch_submit", "dp_batch_poll", "dp_batch_stats"]
