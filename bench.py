@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 # of this workload) from an ncu capture of the current kernel version; see
 # profiles/bellman_tiled_c1_stage79.md.  Reset to None whenever the kernel
 # changes until it is captured again.
-BELLMAN_TRAFFIC_BYTES = 4.04e6
+BELLMAN_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -361,19 +361,24 @@ def run_ours(args):
     pre_ms = statistics.median(x["precompute"] for x in profs)
     sweep_ms = statistics.median(x["sweep"] for x in profs)
     per_launch_s = bell_ms / 1e3 / p.n_stages
-    flops_per_launch = 4.0 * stats["effective_evals"] / p.n_stages  # 2 FMA per feasible state x control
+    # per (state, envelope line): 1 FMA; per (state, torque class): three
+    # two-way blends of J_{k+1} (9 FLOP), the SoC-row difference and the add
+    flops_per_launch = (2.0 * stats["envelope_evals"] + 11.0 * stats["class_evals"]) / p.n_stages
     achieved = flops_per_launch / per_launch_s / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "bellman_tiled", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": BELLMAN_TRAFFIC_BYTES,
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts)",
-                "work_basis": "4 FLOP (2 FMA) per effective state x control evaluation",
+                "work_basis": "2 FLOP per (state, envelope line) FMA + 11 FLOP per (state, torque class) window value",
                 "bellman_ms_per_launch": 1e3 * per_launch_s,
                 "share_of_sweep": bell_ms / sweep_ms if sweep_ms > 0 else None,
                 "precompute_ms_per_launch": pre_ms / p.n_stages,
                 "effective_evals_per_s": stats["effective_evals"] / (bell_ms / 1e3),
-                "tie_states": stats["tie_states"], "argmin_states": stats["argmin_states"]}
+                "envelope_evals_per_launch": stats["envelope_evals"] / p.n_stages,
+                "class_evals_per_launch": stats["class_evals"] / p.n_stages,
+                "envelope_fraction": stats["envelope_evals"] / max(1, stats["effective_evals"]),
+                "argmin_states": stats["argmin_states"]}
 
     # end to end through the public API with host buffers: upload the
     # problem tables, solve, read the trajectory back, every step

@@ -130,10 +130,14 @@ dp_status dp_problem_destroy(dp_problem_t p);
 /* Backward recursion of Eq. (9a)-(9d): J_N = c_T on the grid, then for
  * k = N-1 .. 0 the per-state minimum over all controls of the stage cost
  * plus the trilinearly interpolated J_{k+1} at the successor, with the
- * argmin.  Exact FP32 ties are broken in the order (torque class, control
- * index): the first class of ascending total torque T_eng + T_bsg (brake flag
- * fastest) that reaches the minimum, then the lowest control index inside
- * that class.  Asynchronous on stream;
+ * argmin.  Controls with the same total torque T_eng + T_bsg and brake flag
+ * (a torque class) and the same SoC cell shift read the same two SoC rows of
+ * J_{k+1}; their values are lines c + f D in the difference D of those rows,
+ * and only the lines on the lower envelope of each such group are evaluated
+ * (the minimum is that of all controls up to FP32 rounding).  Exact FP32 ties
+ * are broken in the order (torque class, control index): the first class of
+ * ascending total torque (brake flag fastest) that reaches the minimum, then
+ * the lowest control index inside that class.  Asynchronous on stream;
  * results stay on the device.  The 2N+1 launches are captured in a CUDA graph
  * on the first call on a stream and replayed afterwards. */
 dp_status dp_solve_backward(dp_problem_t p, void *stream);
@@ -228,11 +232,12 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4]);
  * (effective evaluations, summed over stages), out[1] = state x torque-class
  * pairs evaluated, out[2] = bytes one dp_problem_update copies host to
  * device, out[3] = bytes one dp_rollout copies device to host, out[4] =
- * feasible states whose minimum is reached by controls of more than one
- * torque class (exact ties; the tiled kernel then re-evaluates every class to
- * find the lowest winning control), out[5] = feasible states whose argmin the tiled
- * kernel recovered.  DP_ERR_NOT_SOLVED before a sweep. */
-dp_status dp_sweep_stats(dp_problem_t p, int64_t out[6], void *stream);
+ * reserved (0), out[5] = feasible states whose argmin the
+ * tiled kernel recovered, out[6] = state x control pairs the Bellman kernels
+ * evaluate: per torque class and SoC shift only the controls on the lower
+ * envelope of their values (see dp_solve_backward).  DP_ERR_NOT_SOLVED
+ * before a sweep. */
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[7], void *stream);
 
 /* ---- Batches of independent problems ------------------------------------
  *

@@ -304,7 +304,7 @@ dp_status upload_tables(dp_problem *p, cudaStream_t s)
 // stages in backward order.
 dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 {
-    DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s));
+    DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
     DP_CUDA(launch_terminal(p->dP, p->hP, p->V(p->N), s));
     DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, p->N, p->scratch(), s));
     for (int k = p->N - 1; k >= 0; --k)
@@ -458,7 +458,7 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_pi_tmp));
     TRY(dev_alloc_n(p, (size_t)(3 * (P.N + 1) + 3 * P.N + 4), &p->d_roll));
     TRY(dev_alloc_n(p, (size_t)P.N, &p->d_roll_u));
-    TRY(dev_alloc_n(p, (size_t)4, &p->d_stats));
+    TRY(dev_alloc_n(p, (size_t)5, &p->d_stats));
     TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_lam));
     TRY(dev_alloc_n(p, (size_t)8, &p->d_adj));
     TRY(upload_tables(p, p->create_stream));
@@ -527,13 +527,13 @@ dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5])
     return DP_OK;
 }
 
-dp_status dp_sweep_stats(dp_problem_t p, int64_t out[6], void *stream)
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[7], void *stream)
 {
     if (!p || !out)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!p->solved)
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
     cudaStream_t s = (cudaStream_t)stream;
     DP_CUDA(cudaMemcpyAsync(h, p->d_stats, sizeof h, cudaMemcpyDeviceToHost, s));
     DP_CUDA(cudaStreamSynchronize(s));
@@ -544,6 +544,7 @@ dp_status dp_sweep_stats(dp_problem_t p, int64_t out[6], void *stream)
     out[3] = (int64_t)((3 * (p->N + 1) + 3 * p->N + 4) * sizeof(double) + p->N * sizeof(int));
     out[4] = (int64_t)h[2];
     out[5] = (int64_t)h[3];
+    out[6] = (int64_t)h[4] * p->n_xi * p->n_t;
     return DP_OK;
 }
 
@@ -607,7 +608,7 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
         DP_CUDA(cudaEventCreate(&e));
     dp_status st = DP_OK;
     auto run = [&]() -> dp_status {
-        DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s));
+        DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
         DP_CUDA(cudaEventRecord(ev[0], s));
         DP_CUDA(launch_terminal(p->dP, p->hP, p->V(N), s));
         DP_CUDA(cudaEventRecord(ev[1], s));

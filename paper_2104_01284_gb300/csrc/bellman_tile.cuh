@@ -7,24 +7,30 @@
 // axes of the trilinear interpolation are shared by the class and only the
 // SoC axis depends on u (Eq. 5a-5c).  With uniform grids the SoC shift is the
 // same for every j and the time shift the same for every l, so
-//   J_{k+1}(f(x, u)) = w0_u G_C(j + d_u) + w1_u G_C(j + d_u + 1)
+//   J_{k+1}(f(x, u)) = G_C(j + d_u) + f_u (G_C(j + d_u + 1) - G_C(j + d_u))
 // where G_C(j') blends two speed rows and two time columns of J_{k+1} at SoC
-// row j'.  G_C is computed once per class and lane; the per-control work is
-// two FMAs and one min.  At a light stage the arrival check (Eq. 5c, 7c, 8)
-// depends on the arrival time (per lane and class); on the standstill row
-// v = 0 at a light node the departure waits for green, which shifts the time
-// landing per time node.
+// row j'.  For the controls of one class and one shift d the value is
+// G(j + d) + (c_u + f_u D(j + d)) with D the forward difference of G, a line
+// in D: the precompute kernel keeps only each bucket's lower envelope, and
+// the minimum over the bucket is G(j + d) + min over its lines of
+// (c_u + f_u D), one FMA and one min per line and row.  At a light stage the
+// arrival check (Eq. 5c, 7c, 8) depends on the arrival time (per lane and
+// class); on the standstill row v = 0 at a light node the departure waits for
+// green, which shifts the time landing per time node.
 //
 // A tile is one speed row and TLANES lanes; each lane owns one (SoC group of
 // R rows, time node) pair, the pairs of a row laid out back to back so no lane
-// idles on a ragged time axis.  The row's class and control tables are staged
-// in shared memory.  Per class a lane keeps a register window of R + 4
-// blended values; the controls of a class are grouped by SoC shift
-// d in {-2, -1, 0, 1} so window offsets are compile-time constants; two rows go
-// through one packed FP32 FMA (__ffma2_rn) and two controls through one
-// three-input min.  Only class minima are tracked in the sweep; afterwards each
-// warp buckets its states by winning class in shared memory and re-evaluates
-// that class (bit for bit the same arithmetic) to recover the argmin.
+// idles on a ragged time axis.  The row's class and line tables are staged in
+// shared memory.  Per class a lane keeps a register window of blended values
+// G and differences D (the outermost two only when a bucket needs them); the
+// lines of a class are grouped by shift d in {-2, -1, 0, 1} so window offsets
+// are compile-time constants; two rows go through one packed FP32 FMA
+// (__ffma2_rn) and two lines through one three-input min.  Only class minima
+// are tracked in the sweep; afterwards each warp buckets its states by
+// winning class in shared memory and re-evaluates that class (bit for bit the
+// same arithmetic) to recover the argmin.  An arrival during red points the
+// class's time corner at the padding columns, so its values come out
+// infeasible without a per-row select.
 //
 // Argmin order: (value, torque class, control index).  Among controls with
 // exactly equal FP32 values the first class in class order (total torque
@@ -68,7 +74,6 @@ __device__ __forceinline__ float blend(const float *p0, const float *p1, float w
 struct TCtx {
     const float *p0, *p1;  // speed rows iv, iv+1 of J_{k+1} at padded SoC row 0, lower time column
     float wv0, wv1, wt0, wt1;
-    bool red;              // arrival during red: every value of the class is infeasible
 };
 
 struct StageInfo {
@@ -91,9 +96,17 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, c
         snap_split(__fdiv_rn(__fadd_rn(wait, C.dt), P.h_t), st, ft);
         t0 = l + st;
     }
+    // an arrival during red at the next node (Eq. 5c, 7c, 8) makes every
+    // value of the class infeasible: read the padding columns, which hold
+    // V_BIG in every row
+    bool red = false;
+    if (si.next_light >= 0 && C.v1 > 0.f) {
+        const float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
+        red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
+    }
     // a lower corner past the grid reads the padding column n_t; the upper
     // corner is the next column, still inside the row (ld_t >= n_t + 2)
-    const int ta = min(t0, P.n_t);
+    const int ta = red ? P.n_t : min(t0, P.n_t);
     x.wt1 = ft;
     x.wt0 = __fsub_rn(1.f, ft);
     x.wv1 = C.fv;
@@ -101,11 +114,6 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, c
     const size_t vrow = (size_t)P.xi_rows * P.ld_t;
     x.p0 = Vn + (size_t)C.iv * vrow + ta;
     x.p1 = x.p0 + vrow;
-    x.red = false;
-    if (si.next_light >= 0 && C.v1 > 0.f) {
-        float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
-        x.red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
-    }
     return x;
 }
 
@@ -119,14 +127,15 @@ template <bool NC>
 __device__ __forceinline__ float g_at(const DevParams &P, const TCtx &x, int j)
 {
     const int o = row_offset(P, j);
-    const float g = blend<NC>(x.p0 + o, x.p1 + o, x.wv0, x.wv1, x.wt0, x.wt1);
-    return x.red ? V_BIG : g;
+    return blend<NC>(x.p0 + o, x.p1 + o, x.wv0, x.wv1, x.wt0, x.wt1);
 }
 
-// c + w0 g0 + w1 g1, in this order (the packed path rounds identically).
-__device__ __forceinline__ float split_value(const SplitRec &S, float g0, float g1)
+// g0 + (c + f (g1 - g0)), in this order (the tile's bucket path rounds
+// identically: it takes the minimum of c + f D before adding g0, and adding
+// g0 is monotone).
+__device__ __forceinline__ float split_value(float c, float f, float g0, float g1)
 {
-    return __fmaf_rn(S.w1, g1, __fmaf_rn(S.w0, g0, S.c));
+    return __fadd_rn(g0, __fmaf_rn(f, __fsub_rn(g1, g0), c));
 }
 
 __device__ __forceinline__ int split_u(const SplitRec &S) { return (int)(S.bits & 0xffffu); }
@@ -165,47 +174,81 @@ __device__ __forceinline__ float wait_time(const StageTables &tb, int k, float t
     return ph < r ? __fsub_rn(r, ph) : 0.f;
 }
 
-// Minimum over the controls of one SoC-shift bucket: row r uses window values
-// G[r + D + 2] and G[r + D + 3].  EV holds the even-aligned pairs
-// {G[2p], G[2p+1]}, OD the odd-aligned pairs {G[2p+1], G[2p+2]}.
+// Minimum over the lines of one SoC-shift bucket: row r takes
+// min_u (c_u + f_u D[r + D + 2]).  Lines are staged as {c, c, f, f} so each
+// gives its two packed operands directly.  EV holds the even-aligned
+// difference pairs {D[2p], D[2p+1]}, OD the odd-aligned pairs {D[2p+1], D[2p+2]}.
 template <int R, int D>
-__device__ __forceinline__ void bucket_min(const SplitRec *spl, int q, int n, const float2 (&EV)[R / 2 + 2],
+__device__ __forceinline__ void bucket_min(const float4 *ln, int n, const float2 (&EV)[R / 2 + 1],
                                            const float2 (&OD)[R / 2 + 1], float (&cm)[R])
 {
-    const int end = q + n;
-    for (; q + 1 < end; q += 2) {
-        const SplitRec s1 = spl[q], s2 = spl[q + 1];
-        const float2 c1 = make_float2(s1.c, s1.c), w01 = make_float2(s1.w0, s1.w0), w11 = make_float2(s1.w1, s1.w1);
-        const float2 c2 = make_float2(s2.c, s2.c), w02 = make_float2(s2.w0, s2.w0), w12 = make_float2(s2.w1, s2.w1);
+    {
+        const float4 a = ln[0];
+        const float2 c1 = make_float2(a.x, a.y), f1 = make_float2(a.z, a.w);
 #pragma unroll
         for (int p = 0; p < R / 2; ++p) {
-            const float2 LO = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
-            const float2 HI = ((D & 1) == 0) ? OD[p + (D + 2) / 2] : EV[p + (D + 3) / 2];
-            const float2 F1 = __ffma2_rn(w11, HI, __ffma2_rn(w01, LO, c1));
-            const float2 F2 = __ffma2_rn(w12, HI, __ffma2_rn(w02, LO, c2));
+            const float2 DD = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 F1 = __ffma2_rn(f1, DD, c1);
+            cm[2 * p] = F1.x;
+            cm[2 * p + 1] = F1.y;
+        }
+    }
+    int q = 1;
+    for (; q + 1 < n; q += 2) {
+        const float4 a = ln[q], b = ln[q + 1];
+        const float2 c1 = make_float2(a.x, a.y), f1 = make_float2(a.z, a.w);
+        const float2 c2 = make_float2(b.x, b.y), f2 = make_float2(b.z, b.w);
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) {
+            const float2 DD = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 F1 = __ffma2_rn(f1, DD, c1);
+            const float2 F2 = __ffma2_rn(f2, DD, c2);
             cm[2 * p] = min3(cm[2 * p], F1.x, F2.x);
             cm[2 * p + 1] = min3(cm[2 * p + 1], F1.y, F2.y);
         }
     }
-    if (q < end) {
-        const SplitRec s1 = spl[q];
-        const float2 c1 = make_float2(s1.c, s1.c), w01 = make_float2(s1.w0, s1.w0), w11 = make_float2(s1.w1, s1.w1);
+    if (q < n) {
+        const float4 a = ln[q];
+        const float2 c1 = make_float2(a.x, a.y), f1 = make_float2(a.z, a.w);
 #pragma unroll
         for (int p = 0; p < R / 2; ++p) {
-            const float2 LO = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
-            const float2 HI = ((D & 1) == 0) ? OD[p + (D + 2) / 2] : EV[p + (D + 3) / 2];
-            const float2 F1 = __ffma2_rn(w11, HI, __ffma2_rn(w01, LO, c1));
+            const float2 DD = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
+            const float2 F1 = __ffma2_rn(f1, DD, c1);
             cm[2 * p] = fminf(cm[2 * p], F1.x);
             cm[2 * p + 1] = fminf(cm[2 * p + 1], F1.y);
         }
     }
 }
 
+// One bucket's candidates G[r + D + 2] + cm[r] folded into the class minimum
+// (the first bucket of the class initialises it).
+template <int R, int D>
+__device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float (&cm)[R], float (&cls)[R], bool first)
+{
+    float cand[R];
+    if ((D & 1) == 0) {
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) {
+            const float2 s2 = __fadd2_rn(make_float2(G[2 * p + D + 2], G[2 * p + D + 3]),
+                                         make_float2(cm[2 * p], cm[2 * p + 1]));
+            cand[2 * p] = s2.x;
+            cand[2 * p + 1] = s2.y;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            cand[r] = __fadd_rn(G[r + D + 2], cm[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        cls[r] = first ? cand[r] : fminf(cls[r], cand[r]);
+}
+
 // Lowest control index of class E whose value at SoC row j equals bv (INT_MAX
 // if none), re-evaluated with exactly the arithmetic of the sweep.
 template <bool NC>
 __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x, const ClassEntry &E,
-                                              const SplitRec *spl, int j, float bv)
+                                              const float4 *ln, const unsigned short *us, int j, float bv)
 {
     float g5[5];  // SoC rows j - 2 .. j + 2
 #pragma unroll
@@ -216,25 +259,27 @@ __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x,
 #pragma unroll
     for (int b = 0; b < 4; ++b) {  // bucket b holds the shift d = b - 2
         for (int n = 0; n < E.nb[b]; ++n, ++q) {
-            const SplitRec S = spl[q];
-            const int u = split_u(S);
-            if (split_value(S, g5[b], g5[b + 1]) == bv && u < ub)
+            const int u = us[q];
+            if (split_value(ln[q].x, ln[q].z, g5[b], g5[b + 1]) == bv && u < ub)
                 ub = u;
         }
     }
     for (int n = 0; n < E.n_other; ++n, ++q) {
-        const SplitRec S = spl[q];
-        const int d = split_d(S), u = split_u(S);
-        if (split_value(S, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv && u < ub)
+        const float4 a = ln[q];
+        const int d = __float_as_int(a.y), u = us[q];
+        if (split_value(a.x, a.z, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv && u < ub)
             ub = u;
     }
     return ub;
 }
 
-// Shared memory of a tile: the row's tables, then per warp the argmin-recovery
-// buffers: counters [n_cls + 1], entry list [32 R], best value per state [32 R].
+// Shared memory of a tile: the row's tables (classes, class entries, lines as
+// {c, c, f, f} -- {c, d, f, f} for a line outside the four buckets, d as an
+// int bit pattern -- and the lines' control indices), then per warp the
+// argmin-recovery buffers:
+// counters [n_cls + 1], entry list [32 R], best value per state [32 R].
 struct Layout {
-    size_t ent, spl, warp, warp_bytes, total;
+    size_t ent, line, bits, warp, warp_bytes, total;
     size_t w_list, w_best;  // offsets inside a warp's block
 };
 
@@ -245,8 +290,10 @@ __host__ __device__ inline Layout layout(int n_cls, int n_u)
     size_t o = (size_t)n_cls * sizeof(ClassRec);
     L.ent = o;
     o += (size_t)n_cls * sizeof(ClassEntry);
-    L.spl = o;
-    o += (size_t)n_u * sizeof(SplitRec);
+    L.line = o;
+    o += (size_t)n_u * sizeof(float4);
+    L.bits = o;
+    o += ((size_t)n_u * sizeof(unsigned short) + 15) / 16 * 16;
     L.warp = o;
     size_t w = ((size_t)(n_cls + 1) * sizeof(int) + 15) / 16 * 16;
     L.w_list = w;
@@ -279,7 +326,8 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     const Layout L = layout<R>(P.n_cls, P.n_u);
     ClassRec *s_cls = reinterpret_cast<ClassRec *>(smem_raw);
     ClassEntry *s_ent = reinterpret_cast<ClassEntry *>(smem_raw + L.ent);
-    SplitRec *s_spl = reinterpret_cast<SplitRec *>(smem_raw + L.spl);
+    float4 *s_line = reinterpret_cast<float4 *>(smem_raw + L.line);
+    unsigned short *s_u = reinterpret_cast<unsigned short *>(smem_raw + L.bits);
     __syncthreads();  // the previous tile may still read the tables
     {
         const int4 *src = reinterpret_cast<const int4 *>(g_cls);
@@ -290,10 +338,12 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         int4 *dst2 = reinterpret_cast<int4 *>(s_ent);
         for (int q = tid; q < n_ent * 2; q += TLANES)
             dst2[q] = src2[q];
-        const int4 *src3 = reinterpret_cast<const int4 *>(g_spl);
-        int4 *dst3 = reinterpret_cast<int4 *>(s_spl);
-        for (int q = tid; q < n_spl; q += TLANES)
-            dst3[q] = src3[q];
+        for (int q = tid; q < n_spl; q += TLANES) {
+            const SplitRec S = g_spl[q];
+            const int d = split_d(S);
+            s_line[q] = make_float4(S.c, (d >= -2 && d <= 1) ? S.c : __int_as_float(d), S.f, S.f);
+            s_u[q] = (unsigned short)split_u(S);
+        }
     }
     const int warp = tid >> 5, lane = tid & 31;
     unsigned char *wbase = smem_raw + L.warp + warp * L.warp_bytes;
@@ -323,11 +373,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         roff[w] = row_offset(P, jb - 2 + w);
 
     // per row: the running minimum and the first class (in class order)
-    // reaching it; `tie` marks rows whose minimum a later class matches
-    // exactly (counted only: the order (value, class, control) decides)
+    // reaching it (the order (value, class, control) decides exact ties)
     float best[R];
     int bcls[R];
-    unsigned tie = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         best[r] = __int_as_float(0x7f800000);
@@ -336,48 +384,62 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     for (int e = 0; e < n_ent; ++e) {
         const ClassEntry E = s_ent[e];
         const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
+        // window rows jb - 2 .. jb + R + 1; the outermost two only for the
+        // buckets d = -2 and d = +1 (warp-uniform: E is the same in every lane)
         float G[R + 4];
+        float Dg[R + 3];
 #pragma unroll
-        for (int w = 0; w < R + 4; ++w) {
-            const float g = blend<NC>(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
-            G[w] = x.red ? V_BIG : g;
+        for (int w = 1; w < R + 3; ++w)
+            G[w] = blend<NC>(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
+        G[0] = G[R + 3] = 0.f;
+        if (E.nb[0] > 0)
+            G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
+        if (E.nb[3] > 0)
+            G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
+#pragma unroll
+        for (int w = 0; w < R + 3; ++w)
+            Dg[w] = __fsub_rn(G[w + 1], G[w]);
+        float2 EV[R / 2 + 1], OD[R / 2 + 1];
+#pragma unroll
+        for (int p = 0; p < R / 2 + 1; ++p) {
+            EV[p] = make_float2(Dg[2 * p], Dg[2 * p + 1]);
+            OD[p] = make_float2(Dg[2 * p + 1], Dg[2 * p + 2]);
         }
-        float2 EV[R / 2 + 2], OD[R / 2 + 1];
-#pragma unroll
-        for (int p = 0; p < R / 2 + 2; ++p)
-            EV[p] = make_float2(G[2 * p], G[2 * p + 1]);
-#pragma unroll
-        for (int p = 0; p < R / 2 + 1; ++p)
-            OD[p] = make_float2(G[2 * p + 1], G[2 * p + 2]);
+        float cls_min[R];
         float cm[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            cm[r] = __int_as_float(0x7f800000);
+        bool first = true;
         int q = E.off;
-        bucket_min<R, -2>(s_spl, q, E.nb[0], EV, OD, cm);
-        q += E.nb[0];
-        bucket_min<R, -1>(s_spl, q, E.nb[1], EV, OD, cm);
-        q += E.nb[1];
-        bucket_min<R, 0>(s_spl, q, E.nb[2], EV, OD, cm);
-        q += E.nb[2];
-        bucket_min<R, 1>(s_spl, q, E.nb[3], EV, OD, cm);
-        q += E.nb[3];
-        for (int n = 0; n < E.n_other; ++n, ++q) {
-            const SplitRec S = s_spl[q];
-            const int d = split_d(S);
+#define ECODP_BUCKET(B, D)                                      \
+        if (E.nb[B] > 0) {                                      \
+            bucket_min<R, D>(s_line + q, E.nb[B], EV, OD, cm);  \
+            bucket_fold<R, D>(G, cm, cls_min, first);           \
+            first = false;                                      \
+            q += E.nb[B];                                       \
+        }
+        ECODP_BUCKET(0, -2)
+        ECODP_BUCKET(1, -1)
+        ECODP_BUCKET(2, 0)
+        ECODP_BUCKET(3, 1)
+#undef ECODP_BUCKET
+        if (first) {
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                cm[r] = fminf(cm[r],
-                              split_value(S, g_at<NC>(P, x, jb + r + d), g_at<NC>(P, x, jb + r + d + 1)));
+                cls_min[r] = __int_as_float(0x7f800000);
+        }
+        for (int n = 0; n < E.n_other; ++n, ++q) {
+            const float4 a = s_line[q];
+            const int d = __float_as_int(a.y);
+            const float c = a.x, f = a.z;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                cls_min[r] = fminf(cls_min[r],
+                                   split_value(c, f, g_at<NC>(P, x, jb + r + d), g_at<NC>(P, x, jb + r + d + 1)));
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (cm[r] < best[r]) {
-                best[r] = cm[r];
+            if (cls_min[r] < best[r]) {
+                best[r] = cls_min[r];
                 bcls[r] = e;
-                tie &= ~(1u << r);
-            } else if (cm[r] == best[r]) {
-                tie |= 1u << r;
             }
         }
     }
@@ -398,14 +460,10 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 pik[((size_t)i * P.n_xi + j) * P.n_t + l] = -1;
         }
     }
-    tie &= todo;
     if (stats) {
-        const unsigned n_tie = __reduce_add_sync(FULL, (unsigned)__popc(tie));
         const unsigned n_find = __reduce_add_sync(FULL, (unsigned)__popc(todo));
-        if (lane == 0) {
-            atomicAdd(stats + 2, (unsigned long long)n_tie);
+        if (lane == 0)
             atomicAdd(stats + 3, (unsigned long long)n_find);
-        }
     }
 
     // bucket the feasible states by their first winning class and recover the
@@ -459,7 +517,8 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const ClassEntry E = s_ent[e];
         const TCtx x = class_ctx(P, Vn, s_cls[E.cls], lq, tlq, wq, si);
         const int j = jgq * R + r;
-        pik[((size_t)i * P.n_xi + j) * P.n_t + lq] = (int16_t)class_lowest_u<NC>(P, x, E, s_spl, j, w_best[s]);
+        pik[((size_t)i * P.n_xi + j) * P.n_t + lq] =
+            (int16_t)class_lowest_u<NC>(P, x, E, s_line, s_u, j, w_best[s]);
     }
 }
 

@@ -70,19 +70,22 @@ struct ClassRec {
     int pad;
 };
 
-// One feasible control: its stage cost c (Eq. 1/6), its SoC-axis shift d and
-// interpolation weights (w0, w1) of xi' = xi - dt I / C_nom (Eq. 5b), and its
-// index u, packed as bits = u | d << 16.  16 bytes: one vector load.
+// One control of a row's table: its stage cost c (Eq. 1/6), the SoC-axis
+// cell shift d and fraction f of xi' = xi - dt I / C_nom (Eq. 5b), and its
+// index u, packed as bits = u | d << 16.  Its interpolated value at SoC row j
+// is G(j + d) + (c + f (G(j + d + 1) - G(j + d))) with G the speed/time
+// blend of J_{k+1}.  16 bytes: one vector load.
 struct __align__(16) SplitRec {
-    float c, w0, w1;
+    float c, f;
     unsigned bits;
+    unsigned pad;
 };
 
 struct ClassEntry {
     int cls;    // class index
     int off;    // first split record of this class in the row's split array
-    int nb[4];  // splits with soc shift d = -2, -1, 0, +1
-    int n_other;  // splits with any other shift (after the four buckets)
+    int nb[4];  // lower-envelope controls with soc shift d = -2, -1, 0, +1
+    int n_other;  // every control with any other shift (after the four buckets)
     int n_total;
 };
 
@@ -226,9 +229,9 @@ struct StageScratch {
     ClassEntry *ent;  // [slots][n_v][n_cls]
     int *row_cnt;     // [slots][n_v][2] feasible classes, splits
     SplitRec *spl;    // [slots][n_v][n_u]
-    // [4] running totals (may be NULL): feasible (v, u) pairs, feasible
+    // [5] running totals (may be NULL): feasible (v, u) pairs, feasible
     // (v, class) pairs, states whose minimum ties across classes, states
-    // whose argmin was recovered
+    // whose argmin was recovered, (v, u) pairs kept in the tables (envelopes)
     unsigned long long *stats;
 };
 

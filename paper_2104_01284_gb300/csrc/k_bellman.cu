@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
         for (int q = E.off; q < E.off + E.n_total; ++q) {
             const SplitRec S = spl[q];
             const int d = split_d(S), u = split_u(S);
-            const float F = split_value(S, g_at<true>(P, x, j + d), g_at<true>(P, x, j + d + 1));
+            const float F = split_value(S.c, S.f, g_at<true>(P, x, j + d), g_at<true>(P, x, j + d + 1));
             if (F < best || (F == best && e == be && u < bu)) {
                 best = F;
                 bu = u;

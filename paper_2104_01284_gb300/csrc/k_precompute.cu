@@ -116,8 +116,66 @@ __device__ int block_exclusive_scan(int x, int *buf, int &total)
 // shared per-control result
 struct CtrlRec {
     float cost, f;
-    int d, ok;
+    int d, ok;  // ok: 1 feasible, 2 feasible and on its bucket's lower envelope
 };
+
+constexpr int MAX_MEMBERS = 128;  // controls of one torque class (<= min(n_te, n_tm) <= 90)
+
+// Lower envelope of the lines y_u(x) = cost_u + f_u x over all real x, for
+// the feasible members of class c with SoC shift d (bucket d + 2): marks the
+// members on the envelope with ok = 2 and returns their count.  For one
+// state, all controls of the bucket read the same two blended values G_lo,
+// G_hi of J_{k+1} (Eq. 9b), and the interpolated value is
+// G_lo + (cost_u + f_u (G_hi - G_lo)); its minimum over the bucket is
+// G_lo + envelope(G_hi - G_lo).  Lines sorted by slope f descending (ties:
+// lower cost, then lower u, first); a line between two others is dropped only
+// when it lies on or above their lower envelope everywhere by a clear margin,
+// so FP32 rounding never drops a line that is lowest over a real interval.
+__device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, int d, CtrlRec *s_ctrl)
+{
+    short ord[MAX_MEMBERS];
+    int m = 0;
+    for (int ie = mem.ie_lo; ie <= mem.ie_hi && m < MAX_MEMBERS; ++ie) {
+        const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
+        const CtrlRec r = s_ctrl[u];
+        if (!r.ok || r.d != d)
+            continue;
+        // insertion by (f desc, cost asc, u asc); members arrive in increasing u
+        int q = m++;
+        while (q > 0) {
+            const CtrlRec o = s_ctrl[ord[q - 1]];
+            if (o.f > r.f || (o.f == r.f && o.cost <= r.cost))
+                break;
+            ord[q] = ord[q - 1];
+            --q;
+        }
+        ord[q] = (short)u;
+    }
+    short stk[MAX_MEMBERS];
+    int n = 0;
+    for (int q = 0; q < m; ++q) {
+        const int u = ord[q];
+        const CtrlRec C = s_ctrl[u];
+        if (n > 0 && s_ctrl[stk[n - 1]].f == C.f)
+            continue;  // same slope, not lower: never strictly below the kept line
+        while (n >= 2) {
+            const CtrlRec A = s_ctrl[stk[n - 2]], B = s_ctrl[stk[n - 1]];
+            // B is redundant iff x(A, C) <= x(A, B):
+            // (c_C - c_A)(f_A - f_B) <= (c_B - c_A)(f_A - f_C), denominators > 0
+            const float lhs = __fmul_rn(__fsub_rn(C.cost, A.cost), __fsub_rn(A.f, B.f));
+            const float rhs = __fmul_rn(__fsub_rn(B.cost, A.cost), __fsub_rn(A.f, C.f));
+            const float tol = __fmul_rn(1e-5f, __fadd_rn(fabsf(lhs), fabsf(rhs)));
+            if (lhs < __fsub_rn(rhs, tol))
+                --n;
+            else
+                break;
+        }
+        stk[n++] = (short)u;
+    }
+    for (int q = 0; q < n; ++q)
+        s_ctrl[stk[q]].ok = 2;
+    return n;
+}
 
 // Tables of speed row i of stage k (one CTA of 256 threads; P in shared memory).
 __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k, int i, const StageScratch &sc,
@@ -194,22 +252,37 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     }
     __syncthreads();
 
-    // 3. compact the feasible classes and group each class's controls by d
-    int ent_carry = 0, spl_carry = 0;
+    // 3. compact the feasible classes; per class the lower envelope of each
+    // SoC-shift bucket d in {-2, -1, 0, 1}, then every control of any other
+    // shift (rare: one SoC step is far larger than a step's charge change)
+    int ent_carry = 0, spl_carry = 0, feas_carry = 0;
     for (int c0 = 0; c0 < P.n_cls; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
         Members mem = {};
-        int nspl = 0;
+        int nspl = 0, nfeas = 0;
+        int nb[4] = {0, 0, 0, 0};
         if (c < P.n_cls) {
             mem = class_members(P, c);
             const int b = c % P.n_b;
-            for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie)
-                nspl += s_ctrl[(ie * P.n_tm + member_im(mem, ie)) * P.n_b + b].ok;
+            for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
+                const CtrlRec r = s_ctrl[(ie * P.n_tm + member_im(mem, ie)) * P.n_b + b];
+                if (r.ok) {
+                    ++nfeas;
+                    if (r.d < -2 || r.d > 1)
+                        ++nspl;
+                }
+            }
+            if (nfeas > 0)
+                for (int bucket = 0; bucket < 4; ++bucket) {
+                    nb[bucket] = bucket_envelope(P, mem, b, bucket - 2, s_ctrl);
+                    nspl += nb[bucket];
+                }
         }
-        const int feas = nspl > 0 ? 1 : 0;
-        int ent_tot, spl_tot;
+        const int feas = nfeas > 0 ? 1 : 0;
+        int ent_tot, spl_tot, feas_tot;
         const int ent_idx = block_exclusive_scan(feas, scan_buf, ent_tot) + ent_carry;
         const int spl_off = block_exclusive_scan(nspl, scan_buf, spl_tot) + spl_carry;
+        block_exclusive_scan(nfeas, scan_buf, feas_tot);
         if (feas) {
             const int b = c % P.n_b;
             ClassEntry E;
@@ -223,14 +296,11 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
                     const int im = member_im(mem, ie);
                     const int u = (ie * P.n_tm + im) * P.n_b + b;
                     const CtrlRec r = s_ctrl[u];
-                    if (!r.ok)
-                        continue;
                     const bool in4 = r.d >= -2 && r.d <= 1;
-                    if (bucket < 4 ? (r.d != bucket - 2) : in4)
+                    if (bucket < 4 ? (r.ok != 2 || r.d != bucket - 2) : (!r.ok || in4))
                         continue;
-                    const float w0 = __fsub_rn(1.f, r.f);
                     const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(r.d & 0xffff) << 16);
-                    spl_row[pos] = SplitRec{r.cost, w0, r.f, bits};
+                    spl_row[pos] = SplitRec{r.cost, r.f, bits, 0u};
                     ++pos;
                     ++cnt;
                 }
@@ -243,13 +313,15 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         }
         ent_carry += ent_tot;
         spl_carry += spl_tot;
+        feas_carry += feas_tot;
     }
     if (threadIdx.x == 0) {
         sc.row_cnt[2 * row] = ent_carry;
         sc.row_cnt[2 * row + 1] = spl_carry;
         if (sc.stats) {
-            atomicAdd(sc.stats, (unsigned long long)spl_carry);
+            atomicAdd(sc.stats, (unsigned long long)feas_carry);
             atomicAdd(sc.stats + 1, (unsigned long long)ent_carry);
+            atomicAdd(sc.stats + 4, (unsigned long long)spl_carry);
         }
     }
 }
