@@ -204,6 +204,19 @@ dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t k, const fl
  * where an argmin or an interpolation cell changes with theta. */
 dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream);
 
+/* Value-function storage (the adjoint's checkpointing).  every = 0 or 1:
+ * J_k of every stage stays on the device after a solve (the default).
+ * every = K >= 2: the backward sweep keeps only J_0, J_K, J_2K, ... and J_N;
+ * dp_rollout, dp_adjoint and dp_get_value recompute the stages between two
+ * checkpoints, one segment at a time, with the same kernels and per-stage
+ * tables (results bit-identical to the default; the adjoint's FP64 sums may
+ * differ in the last bits from a different atomic order).  The recompute
+ * costs about one extra backward sweep per rollout or adjoint call; value
+ * memory drops from N+1 stages to about N/K + K + 2.  Waits for the device
+ * to be idle, replaces the storage and marks the problem unsolved.
+ * DP_ERR_INVALID_ARG unless 0 <= every <= n_stages. */
+dp_status dp_set_checkpointing(dp_problem_t p, int32_t every);
+
 /* Human-readable name of a status, and the last error message of the
  * calling thread (empty string if none). */
 const char *dp_status_string(dp_status s);

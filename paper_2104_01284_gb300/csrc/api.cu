@@ -18,9 +18,10 @@ using namespace ecodp::host;
 
 namespace ecodp {
 size_t bellman_smem_bytes(const DevParams &hP);
-cudaError_t launch_adjoint(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
-                           size_t stage_elems, const int16_t *piall, size_t pi_elems, double *lam, double x0,
-                           double xi0, double t0, double *out, cudaStream_t s);
+cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const float *V0, double *lam, double x0,
+                                double xi0, double t0, double *out, cudaStream_t s);
+cudaError_t launch_adjoint_stage(const DevParams *dP, const DevParams &hP, StageTables tb, int k, const float *Vn,
+                                 const int16_t *pik, double *lam, double *out, cudaStream_t s);
 
 namespace host {
 
@@ -78,7 +79,35 @@ struct dp_problem {
 
     StageTables tables() const { return StageTables{d_grade, d_lon, d_cyc, d_red, d_off}; }
     StageScratch scratch() const { return StageScratch{d_cls, d_ent, d_rowcnt, d_spl, d_stats}; }
-    float *V(int k) const { return d_V + (size_t)k * stage_elems; }
+    // Value-function storage.  ckpt == 0: every stage k at d_V + k stage_elems.
+    // ckpt = K >= 2: only stages 0, K, 2K, ... and N are kept (checkpoints,
+    // in that order in d_V); the backward sweep writes the other stages to
+    // two ring slots, and readers recompute a segment (cK, min((c+1)K, N))
+    // from its upper checkpoint into d_seg.
+    int ckpt = 0;
+    float *d_ring = nullptr, *d_seg = nullptr;
+    bool stored(int k) const { return ckpt == 0 || k % ckpt == 0 || k == N; }
+    // J_k's slot during the backward sweep
+    float *Vsweep(int k) const
+    {
+        if (ckpt == 0)
+            return d_V + (size_t)k * stage_elems;
+        if (k % ckpt == 0)
+            return d_V + (size_t)(k / ckpt) * stage_elems;
+        if (k == N)
+            return d_V + (size_t)(N / ckpt + 1) * stage_elems;
+        return d_ring + (size_t)(k & 1) * stage_elems;
+    }
+    int n_segments() const { return ckpt == 0 ? 1 : (N + ckpt - 1) / ckpt; }
+    int seg_lo(int c) const { return ckpt == 0 ? 0 : c * ckpt; }
+    int seg_hi(int c) const { return ckpt == 0 ? N : std::min((c + 1) * ckpt, N); }
+    // where stages seg_lo(c) + 1 .. seg_hi(c) live once segment c is recomputed
+    StageView seg_view(int c) const
+    {
+        if (ckpt == 0)
+            return StageView::all(d_V, stage_elems);
+        return StageView{d_seg, Vsweep(seg_hi(c)), seg_lo(c) + 1, seg_hi(c), stage_elems};
+    }
     int16_t *pi(int k) const { return d_pi + (size_t)k * pi_elems; }
 };
 
@@ -287,6 +316,77 @@ void release(dp_problem *p)
     p->blocks.clear();
 }
 
+void dev_free(dp_problem *p, void *ptr, size_t bytes)
+{
+    if (!ptr)
+        return;
+    for (size_t q = 0; q < p->blocks.size(); ++q)
+        if (p->blocks[q] == ptr) {
+            p->blocks.erase(p->blocks.begin() + q);
+            break;
+        }
+    if (p->has_alloc)
+        p->alloc.free(ptr, (void *)p->create_stream, p->alloc.ctx);
+    else
+        cudaFreeAsync(ptr, p->create_stream);
+    p->bytes_held -= (bytes + 255) & ~(size_t)255;
+}
+
+size_t v_slots(const dp_problem *p)
+{
+    return p->ckpt == 0 ? (size_t)p->N + 1 : (size_t)(p->N / p->ckpt + 1 + (p->N % p->ckpt ? 1 : 0));
+}
+
+// Value-function storage for the current checkpoint setting; every cell
+// starts as V_BIG (the padding keeps it for the object's life).
+dp_status alloc_value_storage(dp_problem *p)
+{
+    const size_t se = p->stage_elems;
+    dp_status st = dev_alloc_n(p, se * v_slots(p), &p->d_V);
+    if (st != DP_OK)
+        return st;
+    DP_CUDA(launch_fill(p->d_V, se * v_slots(p), V_BIG, p->create_stream));
+    if (p->ckpt > 0) {
+        st = dev_alloc_n(p, se * 2, &p->d_ring);
+        if (st != DP_OK)
+            return st;
+        st = dev_alloc_n(p, se * (size_t)std::max(1, p->ckpt - 1), &p->d_seg);
+        if (st != DP_OK)
+            return st;
+        DP_CUDA(launch_fill(p->d_ring, se * 2, V_BIG, p->create_stream));
+        DP_CUDA(launch_fill(p->d_seg, se * (size_t)std::max(1, p->ckpt - 1), V_BIG, p->create_stream));
+    }
+    return DP_OK;
+}
+
+void free_value_storage(dp_problem *p)
+{
+    const size_t se = p->stage_elems;
+    dev_free(p, p->d_V, se * v_slots(p) * sizeof(float));
+    if (p->ckpt > 0) {
+        dev_free(p, p->d_ring, se * 2 * sizeof(float));
+        dev_free(p, p->d_seg, se * (size_t)std::max(1, p->ckpt - 1) * sizeof(float));
+    }
+    p->d_V = p->d_ring = p->d_seg = nullptr;
+}
+
+// Recompute J_k for the stages strictly inside segment c into d_seg, from
+// the segment's upper checkpoint, with the sweep's own kernels and tables
+// (bit-identical to the values the backward sweep produced).
+dp_status recompute_segment(dp_problem *p, int c, cudaStream_t s)
+{
+    if (p->ckpt == 0)
+        return DP_OK;
+    const int lo = p->seg_lo(c), hi = p->seg_hi(c);
+    const StageView view = p->seg_view(c);
+    StageScratch sc = p->scratch();
+    sc.stats = nullptr;
+    for (int k = hi - 1; k > lo; --k)
+        DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, sc, view.at(k + 1), const_cast<float *>(view.at(k)),
+                               p->d_pi_tmp, p->variant, s));
+    return DP_OK;
+}
+
 dp_status upload_tables(dp_problem *p, cudaStream_t s)
 {
     DP_CUDA(cudaMemcpyAsync(p->dP, &p->hP, sizeof(DevParams), cudaMemcpyHostToDevice, s));
@@ -305,10 +405,10 @@ dp_status upload_tables(dp_problem *p, cudaStream_t s)
 dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 {
     DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
-    DP_CUDA(launch_terminal(p->dP, p->hP, p->V(p->N), s));
+    DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(p->N), s));
     DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, p->N, p->scratch(), s));
     for (int k = p->N - 1; k >= 0; --k)
-        DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->V(k + 1), p->V(k), p->pi(k),
+        DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
                                p->variant, s));
     return DP_OK;
 }
@@ -322,8 +422,13 @@ size_t roll_doubles(int N) { return (size_t)(3 * (N + 1) + 3 * N + 4); }
 
 dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s)
 {
-    DP_CUDA(launch_rollout(p->dP, p->hP, p->tables(), p->d_V, p->stage_elems, x0[0], x0[1], x0[2], p->d_roll,
-                           p->d_roll_u, s));
+    for (int c = 0; c < p->n_segments(); ++c) {
+        dp_status st = recompute_segment(p, c, s);
+        if (st != DP_OK)
+            return st;
+        DP_CUDA(launch_rollout(p->dP, p->tables(), p->seg_view(c), p->seg_lo(c), p->seg_hi(c), x0[0], x0[1], x0[2],
+                               p->d_roll, p->d_roll_u, s));
+    }
     DP_CUDA(cudaMemcpyAsync(h_out, p->d_roll, roll_doubles(p->N) * sizeof(double), cudaMemcpyDeviceToHost, s));
     DP_CUDA(cudaMemcpyAsync(h_u, p->d_roll_u, (size_t)p->N * sizeof(int), cudaMemcpyDeviceToHost, s));
     return DP_OK;
@@ -440,7 +545,7 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, light_cap, &p->d_cyc));
     TRY(dev_alloc_n(p, light_cap, &p->d_red));
     TRY(dev_alloc_n(p, light_cap, &p->d_off));
-    TRY(dev_alloc_n(p, p->stage_elems * (size_t)(p->N + 1), &p->d_V));
+    TRY(alloc_value_storage(p));
     TRY(dev_alloc_n(p, p->pi_elems * (size_t)p->N, &p->d_pi));
     if (P.n_cls > MAX_CLASSES) {
         release(p);
@@ -468,7 +573,6 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
         return DP_OK;
     };
     // every padding cell holds the infeasible sentinel for the object's life
-    TRY(cuda_try(launch_fill(p->d_V, p->stage_elems * (size_t)(p->N + 1), V_BIG, p->create_stream), "fill V"));
     TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
@@ -548,6 +652,30 @@ dp_status dp_sweep_stats(dp_problem_t p, int64_t out[7], void *stream)
     return DP_OK;
 }
 
+dp_status dp_set_checkpointing(dp_problem_t p, int32_t every)
+{
+    if (!p)
+        return fail(DP_ERR_INVALID_ARG, "problem is NULL");
+    if (every < 0 || every > p->N)
+        return fail(DP_ERR_INVALID_ARG, "every must be in [0, n_stages]");
+    const int K = every <= 1 ? 0 : every;
+    if (K == p->ckpt)
+        return DP_OK;
+    // the old storage may still be read by queued work on any stream
+    DP_CUDA(cudaDeviceSynchronize());
+    free_value_storage(p);
+    p->ckpt = K;
+    if (p->gexec)
+        cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    p->solved = false;
+    dp_status st = alloc_value_storage(p);
+    if (st != DP_OK)
+        return st;
+    DP_CUDA(cudaStreamSynchronize(p->create_stream));
+    return DP_OK;
+}
+
 dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant)
 {
     if (!p || (variant != 0 && variant != 1))
@@ -610,12 +738,12 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
     auto run = [&]() -> dp_status {
         DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
         DP_CUDA(cudaEventRecord(ev[0], s));
-        DP_CUDA(launch_terminal(p->dP, p->hP, p->V(N), s));
+        DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(N), s));
         DP_CUDA(cudaEventRecord(ev[1], s));
         DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, N, p->scratch(), s));
         DP_CUDA(cudaEventRecord(ev[2], s));
         for (int k = N - 1, q = 3; k >= 0; --k, ++q) {
-            DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->V(k + 1), p->V(k), p->pi(k),
+            DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
                                    p->variant, s));
             DP_CUDA(cudaEventRecord(ev[q], s));
         }
@@ -653,7 +781,15 @@ dp_status dp_get_value(dp_problem_t p, int32_t stage, float *out, int32_t out_is
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
     cudaStream_t s = (cudaStream_t)stream;
     float *dst = out_is_host ? p->d_dense : out;
-    DP_CUDA(launch_dense_from_pad(p->hP, p->V(stage), dst, s));
+    const float *src = p->Vsweep(stage);
+    if (!p->stored(stage)) {
+        const int c = stage / p->ckpt;
+        dp_status st = recompute_segment(p, c, s);
+        if (st != DP_OK)
+            return st;
+        src = p->seg_view(c).at(stage);
+    }
+    DP_CUDA(launch_dense_from_pad(p->hP, src, dst, s));
     if (out_is_host) {
         DP_CUDA(cudaMemcpyAsync(out, p->d_dense, p->pi_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
         DP_CUDA(cudaStreamSynchronize(s));
@@ -715,8 +851,16 @@ dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], do
     if (!p->solved)
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
     cudaStream_t s = (cudaStream_t)stream;
-    DP_CUDA(launch_adjoint(p->dP, p->hP, p->tables(), p->d_V, p->stage_elems, p->d_pi, p->pi_elems, p->d_lam, x0[0],
-                           x0[1], x0[2], p->d_adj, s));
+    DP_CUDA(launch_adjoint_init(p->dP, p->hP, p->Vsweep(0), p->d_lam, x0[0], x0[1], x0[2], p->d_adj, s));
+    for (int c = 0; c < p->n_segments(); ++c) {
+        dp_status st = recompute_segment(p, c, s);
+        if (st != DP_OK)
+            return st;
+        const StageView view = p->seg_view(c);
+        for (int k = p->seg_lo(c); k < p->seg_hi(c); ++k)
+            DP_CUDA(launch_adjoint_stage(p->dP, p->hP, p->tables(), k, view.at(k + 1), p->pi(k), p->d_lam, p->d_adj,
+                                         s));
+    }
     double h[8];
     DP_CUDA(cudaMemcpyAsync(h, p->d_adj, sizeof h, cudaMemcpyDeviceToHost, s));
     DP_CUDA(cudaStreamSynchronize(s));

@@ -24,6 +24,7 @@
 // stored as V_BIG and reported to callers as +inf.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -262,9 +263,28 @@ cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables
                            const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s);
 cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float *padded, cudaStream_t s);
 cudaError_t launch_dense_from_pad(const DevParams &hP, const float *padded, float *dense, cudaStream_t s);
-cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
-                           size_t stage_elems, double v0, double xi0, double t0, double *out, int *out_u,
-                           cudaStream_t s);
+// Where J_k lives for the stages a launch reads: base + (k - k_base)
+// stage_elems, except stage k_tail, which is at `tail` (a checkpoint after a
+// recomputed segment).
+struct StageView {
+    const float *base;
+    const float *tail;
+    int k_base, k_tail;
+    size_t stage_elems;
+    __host__ __device__ const float *at(int k) const
+    {
+        return k == k_tail ? tail : base + (ptrdiff_t)(k - k_base) * (ptrdiff_t)stage_elems;
+    }
+    __host__ __device__ static StageView all(const float *V, size_t stage_elems)
+    {
+        return StageView{V, nullptr, 0, -1, stage_elems};
+    }
+};
+
+// Forward rollout over stages [k_begin, k_end) (a later segment continues from
+// the state left in `out`; see rollout_body).
+cudaError_t launch_rollout(const DevParams *dP, StageTables tb, const StageView &view, int k_begin, int k_end,
+                           double v0, double xi0, double t0, double *out, int *out_u, cudaStream_t s);
 
 // ---- batched instances (device descriptors in params[b], inst[b]) ----------
 

@@ -247,35 +247,35 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
 
 }  // namespace
 
-cudaError_t launch_adjoint(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
-                           size_t stage_elems, const int16_t *piall, size_t pi_elems, double *lam, double x0,
-                           double xi0, double t0, double *out, cudaStream_t s)
+// lam_0 from x0 and J_0(x0) (out[5]); clears the gradient and both lam halves.
+cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const float *V0, double *lam, double x0,
+                                double xi0, double t0, double *out, cudaStream_t s)
 {
     const size_t n = (size_t)hP.n_v * hP.n_xi * hP.n_t;
     cudaError_t e = cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
     if (e != cudaSuccess)
         return e;
-    e = cudaMemsetAsync(lam, 0, n * sizeof(double), s);
+    e = cudaMemsetAsync(lam, 0, 2 * n * sizeof(double), s);
     if (e != cudaSuccess)
         return e;
-    adjoint_init_kernel<<<1, 1, 0, s>>>(dP, Vall, x0, xi0, t0, lam, out);
-    e = cudaGetLastError();
+    adjoint_init_kernel<<<1, 1, 0, s>>>(dP, V0, x0, xi0, t0, lam, out);
+    return cudaGetLastError();
+}
+
+// One stage of the forward lam sweep: lam_{k+1} from lam_k through pi_k and
+// the interpolation weights on J_{k+1} (Vn), with the stage's gradient terms.
+cudaError_t launch_adjoint_stage(const DevParams *dP, const DevParams &hP, StageTables tb, int k, const float *Vn,
+                                 const int16_t *pik, double *lam, double *out, cudaStream_t s)
+{
+    const size_t n = (size_t)hP.n_v * hP.n_xi * hP.n_t;
+    double *lk = lam + (size_t)(k & 1) * n;
+    double *lk1 = lam + (size_t)((k + 1) & 1) * n;
+    cudaError_t e = cudaMemsetAsync(lk1, 0, n * sizeof(double), s);
     if (e != cudaSuccess)
         return e;
     const int blocks = (int)((n + 255) / 256);
-    for (int k = 0; k < hP.N; ++k) {
-        double *lk = lam + (size_t)(k & 1) * n;
-        double *lk1 = lam + (size_t)((k + 1) & 1) * n;
-        e = cudaMemsetAsync(lk1, 0, n * sizeof(double), s);
-        if (e != cudaSuccess)
-            return e;
-        adjoint_stage_kernel<<<blocks, 256, 0, s>>>(dP, tb, k, Vall + (size_t)(k + 1) * stage_elems,
-                                                    piall + (size_t)k * pi_elems, lk, lk1, out);
-        e = cudaGetLastError();
-        if (e != cudaSuccess)
-            return e;
-    }
-    return cudaSuccess;
+    adjoint_stage_kernel<<<blocks, 256, 0, s>>>(dP, tb, k, Vn, pik, lk, lk1, out);
+    return cudaGetLastError();
 }
 
 }  // namespace ecodp

@@ -101,9 +101,12 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
 
 constexpr int ROLL_THREADS = 512;
 
-// The rollout of one problem by the whole CTA.
-__device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables &tb, const float *__restrict__ Vall,
-                             size_t stage_elems, double v0, double xi0, double t0, double *__restrict__ out,
+// The rollout of one problem by the whole CTA over stages [k_begin, k_end).
+// A later segment continues from the state, fuel, cost and fail stage the
+// previous one left in `out`; the terminal cost is added by the segment
+// that ends at stage N.
+__device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables &tb, const StageView &view,
+                             int k_begin, int k_end, double v0, double xi0, double t0, double *__restrict__ out,
                              int *__restrict__ out_u)
 {
     __shared__ DevParams P;
@@ -112,15 +115,8 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     __shared__ float red_F[ROLL_THREADS / 32];
     __shared__ int red_u[ROLL_THREADS / 32];
     __shared__ int s_fail;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0)
         P = *dP;
-        s_v = (float)v0;
-        s_xi = (float)xi0;
-        s_t = t0;
-        s_fuel = 0.0;
-        s_J = 0.0;
-        s_fail = -1;
-    }
     __syncthreads();
     const int N = P.N;
     double *traj = out;
@@ -129,13 +125,31 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     double *o_fuel = o_wait + N;
     double *o_tot = o_fuel + N;
     if (threadIdx.x == 0) {
-        traj[0] = s_v;
-        traj[1] = s_xi;
-        traj[2] = s_t;
+        if (k_begin == 0) {
+            s_v = (float)v0;
+            s_xi = (float)xi0;
+            s_t = t0;
+            s_fuel = 0.0;
+            s_J = 0.0;
+            s_fail = -1;
+            traj[0] = s_v;
+            traj[1] = s_xi;
+            traj[2] = s_t;
+        } else {
+            s_v = (float)traj[3 * k_begin];
+            s_xi = (float)traj[3 * k_begin + 1];
+            s_t = traj[3 * k_begin + 2];
+            s_fuel = o_tot[0];
+            s_J = o_tot[2];
+            s_fail = (int)o_tot[3];
+        }
     }
-    for (int k = 0; k < N; ++k) {
+    __syncthreads();
+    if (s_fail >= 0)
+        return;  // an earlier segment found no feasible control
+    for (int k = k_begin; k < k_end; ++k) {
         const float v = s_v, xi = s_xi, t = (float)s_t;
-        const float *Vn = Vall + (size_t)(k + 1) * stage_elems;
+        const float *Vn = view.at(k + 1);
         float bF = __int_as_float(0x7f800000);
         int bu = INT_MAX;
         for (int u = threadIdx.x; u < P.n_u; u += blockDim.x) {
@@ -197,19 +211,21 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     }
     if (threadIdx.x == 0) {
         o_tot[0] = s_fuel;
-        o_tot[1] = s_t - t0;
-        o_tot[2] = s_fail >= 0 ? __longlong_as_double(0x7ff0000000000000LL)
-                               : s_J + (double)terminal_cost(P, s_v, s_xi);
+        o_tot[1] = s_t - traj[2];
         o_tot[3] = (double)s_fail;
+        if (s_fail >= 0)
+            o_tot[2] = __longlong_as_double(0x7ff0000000000000LL);
+        else
+            o_tot[2] = k_end == N ? s_J + (double)terminal_cost(P, s_v, s_xi) : s_J;
     }
 }
 
 __global__ void __launch_bounds__(ROLL_THREADS) rollout_kernel(const DevParams *__restrict__ dP, StageTables tb,
-                                                               const float *__restrict__ Vall, size_t stage_elems,
-                                                               double v0, double xi0, double t0,
-                                                               double *__restrict__ out, int *__restrict__ out_u)
+                                                               StageView view, int k_begin, int k_end, double v0,
+                                                               double xi0, double t0, double *__restrict__ out,
+                                                               int *__restrict__ out_u)
 {
-    rollout_body(dP, tb, Vall, stage_elems, v0, xi0, t0, out, out_u);
+    rollout_body(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
 }
 
 // Batched: one CTA per instance; instance b writes its output block at
@@ -221,18 +237,17 @@ __global__ void __launch_bounds__(ROLL_THREADS)
 {
     const int b = blockIdx.x;
     const BatchInst &I = inst[b];
-    rollout_body(params + b, I.tb, I.V, I.stage_elems, x0[3 * b], x0[3 * b + 1], x0[3 * b + 2], out + out_off[b],
+    const StageView view = StageView::all(I.V, I.stage_elems);
+    rollout_body(params + b, I.tb, view, 0, I.N, x0[3 * b], x0[3 * b + 1], x0[3 * b + 2], out + out_off[b],
                  out_u + u_off[b]);
 }
 
 }  // namespace
 
-cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const float *Vall,
-                           size_t stage_elems, double v0, double xi0, double t0, double *out, int *out_u,
-                           cudaStream_t s)
+cudaError_t launch_rollout(const DevParams *dP, StageTables tb, const StageView &view, int k_begin, int k_end,
+                           double v0, double xi0, double t0, double *out, int *out_u, cudaStream_t s)
 {
-    (void)hP;
-    rollout_kernel<<<1, ROLL_THREADS, 0, s>>>(dP, tb, Vall, stage_elems, v0, xi0, t0, out, out_u);
+    rollout_kernel<<<1, ROLL_THREADS, 0, s>>>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
     return cudaGetLastError();
 }
 

@@ -142,3 +142,7 @@ dp_batch_submit = _sig("dp_batch_submit", vp, C.POINTER(ProblemDesc), dbl_p, C.P
 dp_batch_poll = _sig("dp_batch_poll", vp, C.c_uint64, C.POINTER(Trajectory))
 dp_batch_stats = _sig("dp_batch_stats", vp, C.POINTER(C.c_int64))
 EXPORTED += ["dp_batch_create", "dp_batch_destroy", "dp_batch_submit", "dp_batch_poll", "dp_batch_stats"]
+
+# value-function checkpointing (every K stages; 0 = keep every stage)
+dp_set_checkpointing = _sig("dp_set_checkpointing", vp, C.c_int32)
+EXPORTED.append("dp_set_checkpointing")

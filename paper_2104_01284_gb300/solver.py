@@ -127,6 +127,13 @@ class EcoDP:
         del keep
         self.p = p
 
+    def set_checkpointing(self, every: int):
+        """Keep J_k only every `every` stages (0: all stages); rollout,
+        adjoint and value() recompute the stages in between."""
+        with torch.cuda.device(self.device):
+            N.check(N.dp_set_checkpointing(self.h, int(every)), "dp_set_checkpointing")
+        self.checkpoint_every = int(every)
+
     def set_variant(self, variant: str):
         N.check(N.dp_set_kernel_variant(self.h, {"direct": 0, "tiled": 1}[variant]), "dp_set_kernel_variant")
 
@@ -209,14 +216,16 @@ THETA = ("mass", "cda", "crr", "r0", "fuel_scale")
 _SOLVERS = {}
 
 
-def _solver_for(p, device):
+def _solver_for(p, device, checkpoint_every=10):
     """A cached EcoDP for problems of p's sizes on device (re-used through
-    dp_problem_update, so repeated evaluations do not reallocate)."""
-    key = (str(device), p.n_stages, p.n_v, p.n_soc, p.n_t, p.n_te, p.n_tm, p.n_brake, len(p.light_stage),
-           p.te_lo, p.te_hi, p.tm_lo, p.tm_hi)
+    dp_problem_update, so repeated evaluations do not reallocate), storing
+    J_k every `checkpoint_every` stages."""
+    key = (str(device), p.n_stages, p.n_v, p.n_soc, p.n_t, p.n_te, p.n_tm, p.n_brake, p.te_lo, p.te_hi, p.tm_lo,
+           p.tm_hi, checkpoint_every)
     dp = _SOLVERS.get(key)
     if dp is None:
         dp = EcoDP(p, device=device)
+        dp.set_checkpointing(min(checkpoint_every, p.n_stages))
         _SOLVERS[key] = dp
     else:
         dp.update(p)
@@ -226,15 +235,16 @@ def _solver_for(p, device):
 class EcoDPValue(torch.autograd.Function):
     """J_0(x0; theta), the optimal cost of problem p at x0, as a function of
     theta = (mass, CdA, Crr, R0, fuel_scale) (a float64 tensor of 5).  The
-    forward pass solves the backward recursion on the GPU; the backward pass
-    returns the adjoint gradient (dp_adjoint)."""
+    forward pass solves the backward recursion on the GPU keeping J_k every
+    `checkpoint_every` stages (10 by default); the backward pass returns the
+    adjoint gradient (dp_adjoint), which recomputes the stages in between."""
 
     @staticmethod
-    def forward(ctx, theta, p, x0=None, device=None):
+    def forward(ctx, theta, p, x0=None, device=None, checkpoint_every=10):
         th = theta.detach().to("cpu", torch.float64).tolist()
         q = p.replace(**dict(zip(THETA, th)))
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        dp = _solver_for(q, dev)
+        dp = _solver_for(q, dev, checkpoint_every)
         dp.solve()
         J, g = dp.adjoint(x0)
         ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
@@ -243,7 +253,7 @@ class EcoDPValue(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
-        return grad_out * g, None, None, None
+        return grad_out * g, None, None, None, None
 
 
 def _trajectory_buffers(n):
