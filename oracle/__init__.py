@@ -66,6 +66,8 @@ class _Problem(C.Structure):
         ("cycle", C.c_void_p), ("red", C.c_void_p), ("offset", C.c_void_p),
         ("fp_band", C.c_double), ("phase_band", C.c_double),
         ("v_off", C.c_void_p), ("xi_off", C.c_void_p), ("t_off", C.c_void_p), ("V_off", C.c_void_p),
+        ("light_model", C.c_int32), ("torque_limits", C.c_int32),
+        ("te_max_coef", C.c_double * 3), ("bsg_power_max", C.c_double),
     ]
 
 
@@ -169,6 +171,13 @@ class OracleProblem:
         s.xi_off = keep("xo", cum([g[1].size for g in self.grids]))
         s.t_off = keep("to", cum([g[2].size for g in self.grids]))
         s.V_off = keep("Vo", cum([int(np.prod(sh)) for sh in self.shapes]))
+        # paper variants (absent attributes: the default readings)
+        s.light_model = int(getattr(p, "light_model", 0))
+        s.torque_limits = int(getattr(p, "torque_limits", 0))
+        coef = getattr(p, "te_max_coef", (0.0, 0.0, 0.0))
+        for i in range(3):
+            s.te_max_coef[i] = float(coef[i])
+        s.bsg_power_max = float(getattr(p, "bsg_power_max", 0.0))
         self.s = s
         self.ref = C.byref(s)
 

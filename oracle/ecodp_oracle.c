@@ -87,6 +87,17 @@ typedef struct {
     /* prefix sums of the per-stage sizes: node arrays (N+1 entries each) and
      * value arrays (N+2 entries, stage k at V_off[k]) */
     const int64_t *v_off, *xi_off, *t_off, *V_off;
+    /* paper variants (0 = the default readings):
+     * light_model 1: the green indicator sampled on the time grid (Sec. III,
+     *   Eq. 8): at a light node, every state with v > 0 at a red time node is
+     *   infeasible, and arrivals are not checked at the continuous time;
+     * torque_limits 1: speed-dependent torque limits (Eq. 7e, 7f),
+     *   T_eng <= c0 + c1 w + c2 w^2 and |T_bsg| w <= bsg_power_max, with w the
+     *   engine (= BSG) speed at the stage-start speed. */
+    int32_t light_model;
+    int32_t torque_limits;
+    double te_max_coef[3];
+    double bsg_power_max;
 } orc_problem;
 
 typedef struct {
@@ -175,6 +186,18 @@ static int transition(const orc_problem *P, int k, double v, double xi, double t
     double F_tr = (Te + Tm) * ratio - (b ? M * P->brake_decel : 0.0);
     double a = (F_tr - F_road) / M;
     double ea = P->fp_band * (fabs(F_tr) + fabs(F_road)) / M;
+    double w = v * ratio;
+
+    /* Eq. (7e), (7f) with speed-dependent limits (variant) */
+    if (P->torque_limits) {
+        const double *c = P->te_max_coef;
+        double te_max = c[0] + c[1] * w + c[2] * w * w;
+        if (decide(d, Te > te_max, fabs(Te - te_max) <= P->fp_band * (fabs(Te) + fabs(te_max) + 1.0)))
+            return 0;
+        double pm = fabs(Tm) * w;
+        if (decide(d, pm > P->bsg_power_max, fabs(pm - P->bsg_power_max) <= P->fp_band * (pm + P->bsg_power_max + 1.0)))
+            return 0;
+    }
 
     /* Eq. (7d): comfort acceleration limits */
     if (decide(d, a < P->a_min, fabs(a - P->a_min) <= ea))
@@ -219,15 +242,15 @@ static int transition(const orc_problem *P, int k, double v, double xi, double t
     double t1 = t + wait + dt;
 
     /* Eq. (5c), (7c), (8): no arrival at a light node during red unless
-     * stopped at the line; evaluated at the continuous arrival time. */
-    if (next_light >= 0 && v1 > 0.0) {
+     * stopped at the line; evaluated at the continuous arrival time (with the
+     * sampled indicator the value function carries the constraint instead). */
+    if (P->light_model == 0 && next_light >= 0 && v1 > 0.0) {
         double ph = phase_of(P, next_light, t1);
         if (decide(d, ph < P->red[next_light], phase_fragile(P, next_light, ph)))
             return 0;
     }
 
     /* powertrain: fuel map and BSG power */
-    double w = v * ratio;
     double mf = 0.0;
     if (Te > 0.0) {
         const double *c = P->fuel_coef;
@@ -508,6 +531,22 @@ int orc_stage(const orc_problem *P, int k, int mode, const double *Vnext, int64_
                         sec = F;
                     }
                 }
+        /* sampled green indicator (variant): a state moving through a light
+         * node at a red time node is infeasible; a time node within the phase
+         * band of a boundary is fragile (green when lenient, red when strict) */
+        int lk = P->light_model == 1 ? light_at(P, k) : -1;
+        if (lk >= 0 && v > 0.0) {
+            double ph = phase_of(P, lk, t);
+            int red = ph < P->red[lk];
+            if (phase_fragile(P, lk, ph) && mode != ORC_NOMINAL) {
+                red = mode == ORC_STRICT;
+                nf_total += 1;
+            }
+            if (red) {
+                best = INFINITY;
+                sec = INFINITY;
+            }
+        }
         Vout[q] = best;
         if (pi)
             pi[q] = isinf(best) ? -1 : bu;
@@ -842,6 +881,11 @@ double orc_sequence_cost(const orc_problem *P, const double *x0, const int32_t *
         const double *tn = P->t_nodes + P->t_off[s1];
         if (tr.v1 < vn[0] || tr.v1 > vn[P->nv[s1] - 1] || tr.xi1 < xn[0] || tr.xi1 > xn[P->nxi[s1] - 1] ||
             tr.t1 < tn[0] || tr.t1 > tn[P->nt[s1] - 1])
+            return INFINITY;
+        /* a path through a light node must meet it green, whichever way the
+         * DP enforces it (continuous arrival check or sampled indicator) */
+        int lj = light_at(P, s1);
+        if (P->light_model == 1 && lj >= 0 && tr.v1 > 0.0 && orc_is_red(P, lj, tr.t1))
             return INFINITY;
         J += tr.cost;
         v = tr.v1;

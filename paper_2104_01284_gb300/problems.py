@@ -117,6 +117,16 @@ class Problem:
     offset: np.ndarray = field(default_factory=lambda: np.zeros(0))
     # initial state for rollout / adjoint
     x0: tuple = (10.0, 0.55, 0.0)
+    # paper variants (0 = the default readings):
+    # light_model 1: green indicator sampled on the time grid (Sec. III, Eq. 8)
+    light_model: int = 0
+    # torque_limits 1: speed-dependent limits (Eq. 7e, 7f): engine torque
+    # <= c0 + c1 w + c2 w^2 and BSG power |T_bsg| w <= bsg_power_max, with w
+    # the crank speed (rad/s).  The default curve peaks near 200 Nm at
+    # w = 180 rad/s; 12 kW caps the BSG above w = 120 rad/s.
+    torque_limits: int = 0
+    te_max_coef: np.ndarray = field(default_factory=lambda: np.array([120.0, 0.9, -0.0025]))
+    bsg_power_max: float = 12000.0
 
     # -- derived sizes ---------------------------------------------------
     @property
@@ -147,7 +157,7 @@ class Problem:
 
     def copy(self) -> "Problem":
         p = dataclasses.replace(self)
-        for f in ("grade", "fuel_coef", "light_stage", "cycle", "red", "offset"):
+        for f in ("grade", "fuel_coef", "light_stage", "cycle", "red", "offset", "te_max_coef"):
             setattr(p, f, np.array(getattr(self, f), copy=True))
         return p
 
