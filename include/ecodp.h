@@ -90,6 +90,15 @@ typedef struct dp_problem_desc {
     int32_t n_lights;     /* traffic lights (Fig. 3) */
     const int32_t *light_stage; /* [n_lights] distinct nodes in [1, n_stages - 1] */
     const double *cycle, *red, *offset; /* [n_lights] s; red iff ((t - offset) mod cycle) < red */
+    /* Paper variants; 0 selects the default reading. */
+    int32_t light_model;  /* 0: an arrival at a light node with v' > 0 is checked at its continuous
+                             time; 1: the green indicator sampled on the time grid (Sec. III, Eq. 8):
+                             at a light node every state with v > 0 at a red time node is
+                             infeasible, and arrivals are not checked otherwise */
+    int32_t torque_limits; /* 0: the torque grids are the limits; 1: speed-dependent limits
+                              (Eq. 7e, 7f) at the stage-start crank speed w = v gear / r_wheel */
+    double te_max_coef[3]; /* torque_limits = 1: T_eng <= c0 + c1 w + c2 w^2 (Nm, w in rad/s) */
+    double bsg_power_max;  /* torque_limits = 1: |T_bsg| w <= bsg_power_max (W, >= 0) */
 } dp_problem_desc;
 
 typedef struct dp_problem *dp_problem_t;

@@ -162,6 +162,14 @@ dp_status validate(const dp_problem_desc *d)
     for (int q = 0; q < d->n_stages; ++q)
         if (!std::isfinite(d->grade[q]) || std::fabs(d->grade[q]) > 1.0)
             return fail(DP_ERR_INVALID_ARG, "grade must be finite with |grade| <= 1");
+    if (d->light_model != 0 && d->light_model != 1)
+        return fail(DP_ERR_INVALID_ARG, "light_model must be 0 or 1");
+    if (d->torque_limits != 0 && d->torque_limits != 1)
+        return fail(DP_ERR_INVALID_ARG, "torque_limits must be 0 or 1");
+    if (d->torque_limits &&
+        (!finite_all({d->te_max_coef[0], d->te_max_coef[1], d->te_max_coef[2], d->bsg_power_max}) ||
+         d->bsg_power_max < 0))
+        return fail(DP_ERR_INVALID_ARG, "torque limits need finite coefficients and bsg_power_max >= 0");
     if (d->n_lights < 0 || d->n_lights > d->n_stages)
         return fail(DP_ERR_INVALID_ARG, "bad n_lights");
     if (d->n_lights > 0 && (!d->light_stage || !d->cycle || !d->red || !d->offset))
@@ -238,6 +246,11 @@ void fill_params(const dp_problem_desc *d, DevParams &P)
     P.w_soc = f32(d->w_soc);
     P.v_ref = f32(d->v_ref);
     P.w_v = f32(d->w_v);
+    P.light_model = d->light_model;
+    P.torque_limits = d->torque_limits;
+    for (int q = 0; q < 3; ++q)
+        P.te_max_c[q] = d->torque_limits ? f32(d->te_max_coef[q]) : 0.f;
+    P.bsg_pmax = d->torque_limits ? f32(d->bsg_power_max) : 0.f;
 }
 
 void fill_tables(const dp_problem_desc *d, HostTables &t)

@@ -78,6 +78,7 @@ struct TCtx {
 
 struct StageInfo {
     bool wait_row;   // v_i == 0 at a light node: wait for green before departing
+    int here;        // light index at node k, or -1
     int next_light;  // light index at node k+1, or -1
     float cyc1, red1, off1;
 };
@@ -100,7 +101,7 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, c
     // value of the class infeasible: read the padding columns, which hold
     // V_BIG in every row
     bool red = false;
-    if (si.next_light >= 0 && C.v1 > 0.f) {
+    if (P.light_model == 0 && si.next_light >= 0 && C.v1 > 0.f) {
         const float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
         red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
     }
@@ -152,6 +153,7 @@ __device__ __forceinline__ StageInfo stage_info(const StageTables &tb, int k, fl
 {
     StageInfo si;
     int lk = tb.light_of_node[k];
+    si.here = lk;
     si.wait_row = (lk >= 0) && (v == 0.f);
     si.next_light = tb.light_of_node[k + 1];
     si.cyc1 = si.red1 = si.off1 = 0.f;
@@ -161,6 +163,16 @@ __device__ __forceinline__ StageInfo stage_info(const StageTables &tb, int k, fl
         si.off1 = tb.offset[si.next_light];
     }
     return si;
+}
+
+// Green indicator sampled on the time grid (light_model 1, Sec. III, Eq. 8):
+// a state moving through the light at node k at a red time node t_l is
+// infeasible.
+__device__ __forceinline__ bool sampled_red(const DevParams &P, const StageTables &tb, const StageInfo &si, float v,
+                                            float tl)
+{
+    return P.light_model == 1 && si.here >= 0 && v > 0.f &&
+           phase_pos(tl, tb.offset[si.here], tb.cycle[si.here]) < tb.red[si.here];
 }
 
 // Standstill time at a red light before departing from (v = 0, t) at node k.
@@ -445,12 +457,13 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     }
 
     // values now; argmin recovery below
+    const bool masked = sampled_red(P, tb, si, v, tl);
     unsigned todo = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int j = jb + r;
         const bool valid = f_ok && j < P.n_xi;
-        const bool feas = valid && best[r] < V_FEAS_MAX;
+        const bool feas = valid && !masked && best[r] < V_FEAS_MAX;
         if (feas)
             todo |= 1u << r;
         if (valid) {

@@ -55,7 +55,22 @@ struct DevParams {
     float fc[6];
     float fuel_scale, gamma;
     float soc_ref, w_soc, v_ref, w_v;
+    // paper variants (see dp_problem_desc)
+    int light_model;    // 1: green indicator sampled on the time grid
+    int torque_limits;  // 1: speed-dependent torque limits
+    float te_max_c[3], bsg_pmax;
 };
+
+// Speed-dependent torque limits (Eq. 7e, 7f) at crank speed w; true if the
+// control (Te, Tm) is allowed.
+__device__ __forceinline__ bool torque_allowed(const DevParams &P, float w, float Te, float Tm)
+{
+    if (!P.torque_limits)
+        return true;
+    const float te_max =
+        __fadd_rn(__fadd_rn(P.te_max_c[0], __fmul_rn(P.te_max_c[1], w)), __fmul_rn(__fmul_rn(P.te_max_c[2], w), w));
+    return !(Te > te_max) && !(__fmul_rn(fabsf(Tm), w) > P.bsg_pmax);
+}
 
 // A torque class: all controls with the same total torque T_eng + T_bsg and
 // brake flag share the speed update (Eq. 5a) and the step time (Eq. 2), hence

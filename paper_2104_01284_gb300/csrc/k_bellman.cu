@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     }
     const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
     const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + l;
-    if (!(best < V_FEAS_MAX)) {
+    if (!(best < V_FEAS_MAX) || sampled_red(P, tb, si, v, tl)) {
         Vk[o] = V_BIG;
         pik[op] = -1;
     } else {

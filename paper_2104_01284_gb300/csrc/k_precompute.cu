@@ -241,10 +241,11 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         CtrlRec r = {0.f, 0.f, 0, 0};
         float I;
         const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
-        if (C.ok && battery_current(P, w, Tm, I)) {
+        const float Te = node_val(P.te_lo, P.te_span, ie, P.n_te);
+        if (C.ok && torque_allowed(P, w, Te, Tm) && battery_current(P, w, Tm, I)) {
             const float dxi = __fdiv_rn(__fmul_rn(C.dt, I), P.cap);
             snap_split(__fdiv_rn(-dxi, P.h_xi), r.d, r.f);
-            const float mf = fuel_rate(P, w, node_val(P.te_lo, P.te_span, ie, P.n_te));
+            const float mf = fuel_rate(P, w, Te);
             r.cost = __fmul_rn(__fadd_rn(__fmul_rn(P.gamma, mf), one_m_gamma), C.dt);
             r.ok = 1;
         }

@@ -82,9 +82,12 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
             wait = __fsub_rn(tb.red[lk], ph);
     }
     const float t1 = __fadd_rn(__fadd_rn(t, wait), dt);
-    if (nl >= 0 && v1 > 0.f && phase_pos(t1, tb.offset[nl], tb.cycle[nl]) < tb.red[nl])
+    // with the sampled indicator the value function carries the light constraint
+    if (P.light_model == 0 && nl >= 0 && v1 > 0.f && phase_pos(t1, tb.offset[nl], tb.cycle[nl]) < tb.red[nl])
         return false;
     const float w = __fmul_rn(v, P.ratio);
+    if (!torque_allowed(P, w, Te, Tm))
+        return false;
     float I;
     if (!battery_current(P, w, Tm, I))
         return false;

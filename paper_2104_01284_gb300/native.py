@@ -50,6 +50,8 @@ class ProblemDesc(C.Structure):
         ("soc_ref", C.c_double), ("w_soc", C.c_double), ("v_ref", C.c_double), ("w_v", C.c_double),
         ("n_lights", C.c_int32), ("light_stage", C.POINTER(C.c_int32)),
         ("cycle", dbl_p), ("red", dbl_p), ("offset", dbl_p),
+        ("light_model", C.c_int32), ("torque_limits", C.c_int32),
+        ("te_max_coef", C.c_double * 3), ("bsg_power_max", C.c_double),
     ]
 
 

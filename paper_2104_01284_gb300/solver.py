@@ -45,6 +45,12 @@ def make_desc(p):
     d.cycle = arr(p.cycle, np.float64, C.c_double)
     d.red = arr(p.red, np.float64, C.c_double)
     d.offset = arr(p.offset, np.float64, C.c_double)
+    d.light_model = int(getattr(p, "light_model", 0))
+    d.torque_limits = int(getattr(p, "torque_limits", 0))
+    coef = getattr(p, "te_max_coef", (0.0, 0.0, 0.0))
+    for q in range(3):
+        d.te_max_coef[q] = float(coef[q])
+    d.bsg_power_max = float(getattr(p, "bsg_power_max", 0.0))
     return d, keep
 
 
