@@ -191,12 +191,12 @@ __device__ __forceinline__ float wait_time(const StageTables &tb, int k, float t
 // gives its two packed operands directly.  EV holds the even-aligned
 // difference pairs {D[2p], D[2p+1]}, OD the odd-aligned pairs {D[2p+1], D[2p+2]}.
 template <int R, int D>
-__device__ __forceinline__ void bucket_min(const float4 *ln, int n, const float2 (&EV)[R / 2 + 1],
+__device__ __forceinline__ void bucket_min(const float2 *ln, int n, const float2 (&EV)[R / 2 + 1],
                                            const float2 (&OD)[R / 2 + 1], float (&cm)[R])
 {
     {
-        const float4 a = ln[0];
-        const float2 c1 = make_float2(a.x, a.y), f1 = make_float2(a.z, a.w);
+        const float2 a = ln[0];
+        const float2 c1 = make_float2(a.x, a.x), f1 = make_float2(a.y, a.y);
 #pragma unroll
         for (int p = 0; p < R / 2; ++p) {
             const float2 DD = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
@@ -207,9 +207,9 @@ __device__ __forceinline__ void bucket_min(const float4 *ln, int n, const float2
     }
     int q = 1;
     for (; q + 1 < n; q += 2) {
-        const float4 a = ln[q], b = ln[q + 1];
-        const float2 c1 = make_float2(a.x, a.y), f1 = make_float2(a.z, a.w);
-        const float2 c2 = make_float2(b.x, b.y), f2 = make_float2(b.z, b.w);
+        const float2 a = ln[q], b = ln[q + 1];
+        const float2 c1 = make_float2(a.x, a.x), f1 = make_float2(a.y, a.y);
+        const float2 c2 = make_float2(b.x, b.x), f2 = make_float2(b.y, b.y);
 #pragma unroll
         for (int p = 0; p < R / 2; ++p) {
             const float2 DD = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
@@ -220,8 +220,8 @@ __device__ __forceinline__ void bucket_min(const float4 *ln, int n, const float2
         }
     }
     if (q < n) {
-        const float4 a = ln[q];
-        const float2 c1 = make_float2(a.x, a.y), f1 = make_float2(a.z, a.w);
+        const float2 a = ln[q];
+        const float2 c1 = make_float2(a.x, a.x), f1 = make_float2(a.y, a.y);
 #pragma unroll
         for (int p = 0; p < R / 2; ++p) {
             const float2 DD = ((D & 1) == 0) ? EV[p + (D + 2) / 2] : OD[p + (D + 1) / 2];
@@ -260,7 +260,8 @@ __device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float
 // if none), re-evaluated with exactly the arithmetic of the sweep.
 template <bool NC>
 __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x, const ClassEntry &E,
-                                              const float4 *ln, const unsigned short *us, int j, float bv)
+                                              const float2 *ln, const unsigned short *us, const SplitRec *g_spl,
+                                              int j, float bv)
 {
     float g5[5];  // SoC rows j - 2 .. j + 2
 #pragma unroll
@@ -272,23 +273,22 @@ __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x,
     for (int b = 0; b < 4; ++b) {  // bucket b holds the shift d = b - 2
         for (int n = 0; n < E.nb[b]; ++n, ++q) {
             const int u = us[q];
-            if (split_value(ln[q].x, ln[q].z, g5[b], g5[b + 1]) == bv && u < ub)
+            if (split_value(ln[q].x, ln[q].y, g5[b], g5[b + 1]) == bv && u < ub)
                 ub = u;
         }
     }
     for (int n = 0; n < E.n_other; ++n, ++q) {
-        const float4 a = ln[q];
-        const int d = __float_as_int(a.y), u = us[q];
-        if (split_value(a.x, a.z, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv && u < ub)
+        const float2 a = ln[q];
+        const int d = split_d(g_spl[q]), u = us[q];
+        if (split_value(a.x, a.y, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv && u < ub)
             ub = u;
     }
     return ub;
 }
 
 // Shared memory of a tile: the row's tables (classes, class entries, lines as
-// {c, c, f, f} -- {c, d, f, f} for a line outside the four buckets, d as an
-// int bit pattern -- and the lines' control indices), then per warp the
-// argmin-recovery buffers:
+// {c, f} and their control indices; a line outside the four buckets reads its
+// shift from the global table), then per warp the argmin-recovery buffers:
 // counters [n_cls + 1], entry list [32 R], best value per state [32 R].
 struct Layout {
     size_t ent, line, bits, warp, warp_bytes, total;
@@ -303,7 +303,7 @@ __host__ __device__ inline Layout layout(int n_cls, int n_u)
     L.ent = o;
     o += (size_t)n_cls * sizeof(ClassEntry);
     L.line = o;
-    o += (size_t)n_u * sizeof(float4);
+    o += ((size_t)n_u * sizeof(float2) + 15) / 16 * 16;
     L.bits = o;
     o += ((size_t)n_u * sizeof(unsigned short) + 15) / 16 * 16;
     L.warp = o;
@@ -326,8 +326,8 @@ __host__ __device__ inline int chunks_per_row(int n_xi, int n_t)
 
 // One tile: speed row i, lane chunk `chunk` of stage k.  The row's tables
 // are (cls, ent, spl) with n_ent feasible classes and n_spl controls.  All
-// TLANES threads of the CTA must call it; it starts and ends with a barrier
-// so the shared memory can be reused by the next tile.
+// TLANES threads of the CTA call it; it starts with a barrier so the shared
+// memory can be reused by the next tile.
 template <int R, bool NC>
 __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, const ClassRec *g_cls,
                              const ClassEntry *g_ent, const SplitRec *g_spl, int n_ent, int n_spl, const float *Vn,
@@ -338,7 +338,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     const Layout L = layout<R>(P.n_cls, P.n_u);
     ClassRec *s_cls = reinterpret_cast<ClassRec *>(smem_raw);
     ClassEntry *s_ent = reinterpret_cast<ClassEntry *>(smem_raw + L.ent);
-    float4 *s_line = reinterpret_cast<float4 *>(smem_raw + L.line);
+    float2 *s_line = reinterpret_cast<float2 *>(smem_raw + L.line);
     unsigned short *s_u = reinterpret_cast<unsigned short *>(smem_raw + L.bits);
     __syncthreads();  // the previous tile may still read the tables
     {
@@ -352,8 +352,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             dst2[q] = src2[q];
         for (int q = tid; q < n_spl; q += TLANES) {
             const SplitRec S = g_spl[q];
-            const int d = split_d(S);
-            s_line[q] = make_float4(S.c, (d >= -2 && d <= 1) ? S.c : __int_as_float(d), S.f, S.f);
+            s_line[q] = make_float2(S.c, S.f);
             s_u[q] = (unsigned short)split_u(S);
         }
     }
@@ -439,9 +438,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 cls_min[r] = __int_as_float(0x7f800000);
         }
         for (int n = 0; n < E.n_other; ++n, ++q) {
-            const float4 a = s_line[q];
-            const int d = __float_as_int(a.y);
-            const float c = a.x, f = a.z;
+            const float2 a = s_line[q];
+            const int d = split_d(g_spl[q]);
+            const float c = a.x, f = a.y;
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 cls_min[r] = fminf(cls_min[r],
@@ -531,7 +530,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const TCtx x = class_ctx(P, Vn, s_cls[E.cls], lq, tlq, wq, si);
         const int j = jgq * R + r;
         pik[((size_t)i * P.n_xi + j) * P.n_t + lq] =
-            (int16_t)class_lowest_u<NC>(P, x, E, s_line, s_u, j, w_best[s]);
+            (int16_t)class_lowest_u<NC>(P, x, E, s_line, s_u, g_spl, j, w_best[s]);
     }
 }
 
