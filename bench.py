@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 # of this workload) from an ncu capture of the current kernel version; see
 # profiles/bellman_tiled_c1_stage79.md.  Reset to None whenever the kernel
 # changes until it is captured again.
-BELLMAN_TRAFFIC_BYTES = None
+BELLMAN_TRAFFIC_BYTES = 3.754496e6
 
 
 def parse():
@@ -419,6 +419,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": config_dict(p, world, "flushed between steps (256 MB write)"),
         "effective_evals_per_s": world * stats["effective_evals"] * args.steps / (total_ms / 1e3),
+        "ms_per_solve_median": statistics.median(times),
+        "ms_per_solve_p99": float(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))]),
         "rollout": {"fuel_g": traj["fuel_g"], "time_s": traj["time_s"], "J": traj["J"]},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks, "adjoint": adjoint, "batched": batched,
