@@ -91,6 +91,7 @@ typedef struct {
      * light_model 1: the green indicator sampled on the time grid (Sec. III,
      *   Eq. 8): at a light node, every state with v > 0 at a red time node is
      *   infeasible, and arrivals are not checked at the continuous time;
+     * light_model 2: the literal standstill step of Eq. (5c) (see transition);
      * torque_limits 1: speed-dependent torque limits (Eq. 7e, 7f),
      *   T_eng <= c0 + c1 w + c2 w^2 and |T_bsg| w <= bsg_power_max, with w the
      *   engine (= BSG) speed at the stage-start speed. */
@@ -205,10 +206,43 @@ static int transition(const orc_problem *P, int k, double v, double xi, double t
     if (decide(d, a > P->a_max, fabs(a - P->a_max) <= ea))
         return 0;
 
+    /* the literal Eq. (5c) (variant light_model 2): standing at a light node,
+     * a control without forward acceleration makes the step at zero speed
+     * while the clock jumps to the end of red (zero time during green); the
+     * engine is off at standstill (start-stop), so only T_eng = 0 realises it.
+     * A departure needs green; there is no folded wait. */
+    int lk = light_at(P, k);
+    if (P->light_model == 2 && lk >= 0 && v == 0.0) {
+        double ph = phase_of(P, lk, t);
+        int red = decide(d, ph < P->red[lk], phase_fragile(P, lk, ph));
+        double R0 = 2.0 * P->ds * a;
+        double eR0 = P->fp_band * 2.0 * P->ds * fabs(a);
+        if (decide(d, R0 <= 0.0, fabs(R0) <= eR0)) {
+            if (Te != 0.0)
+                return 0;
+            double t_rg = 0.0;
+            if (red) { /* a fragile boundary taken as red: the red that has just begun or is about to */
+                if (ph < P->red[lk])
+                    t_rg = P->red[lk] - ph;
+                else if (ph > 0.5 * (P->red[lk] + P->cycle[lk]))
+                    t_rg = P->red[lk] + (P->cycle[lk] - ph);
+            }
+            o->v1 = 0.0;
+            o->xi1 = xi;
+            o->t1 = t + t_rg;
+            o->dt = 0.0;
+            o->wait = t_rg;
+            o->fuel_rate = 0.0;
+            o->cost = (1.0 - P->gamma) * t_rg;
+            return 1;
+        }
+        if (red)
+            return 0;
+    }
+
     /* waiting for green when standing at a light node */
     double wait = 0.0;
-    int lk = light_at(P, k);
-    if (lk >= 0 && v == 0.0) {
+    if (P->light_model != 2 && lk >= 0 && v == 0.0) {
         double ph = phase_of(P, lk, t);
         int red = ph < P->red[lk];
         if (decide(d, red, phase_fragile(P, lk, ph))) {
@@ -244,7 +278,7 @@ static int transition(const orc_problem *P, int k, double v, double xi, double t
     /* Eq. (5c), (7c), (8): no arrival at a light node during red unless
      * stopped at the line; evaluated at the continuous arrival time (with the
      * sampled indicator the value function carries the constraint instead). */
-    if (P->light_model == 0 && next_light >= 0 && v1 > 0.0) {
+    if (P->light_model != 1 && next_light >= 0 && v1 > 0.0) {
         double ph = phase_of(P, next_light, t1);
         if (decide(d, ph < P->red[next_light], phase_fragile(P, next_light, ph)))
             return 0;

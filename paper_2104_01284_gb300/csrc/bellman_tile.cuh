@@ -101,7 +101,7 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, c
     // value of the class infeasible: read the padding columns, which hold
     // V_BIG in every row
     bool red = false;
-    if (P.light_model == 0 && si.next_light >= 0 && C.v1 > 0.f) {
+    if (P.light_model != 1 && si.next_light >= 0 && C.v1 > 0.f) {
         const float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
         red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
     }

@@ -83,7 +83,7 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
     }
     const float t1 = __fadd_rn(__fadd_rn(t, wait), dt);
     // with the sampled indicator the value function carries the light constraint
-    if (P.light_model == 0 && nl >= 0 && v1 > 0.f && phase_pos(t1, tb.offset[nl], tb.cycle[nl]) < tb.red[nl])
+    if (P.light_model != 1 && nl >= 0 && v1 > 0.f && phase_pos(t1, tb.offset[nl], tb.cycle[nl]) < tb.red[nl])
         return false;
     const float w = __fmul_rn(v, P.ratio);
     if (!torque_allowed(P, w, Te, Tm))

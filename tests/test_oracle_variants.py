@@ -163,3 +163,84 @@ def test_sampled_indicator_bruteforce(cfg):
     g0 = exact_grids(p, p.x0)
     V0s, _, _ = O.solve(O.make(p, grids=g0))
     assert V0s[0][0, 0, 0] == pytest.approx(best, rel=1e-12, abs=0)
+
+
+# -- literal standstill step of Eq. (5c) -------------------------------------------
+
+def test_literal_standstill_step_closed_form():
+    """From standstill at a light node: a control without forward
+    acceleration and with the engine off makes the step at zero speed, the
+    clock jumping to the end of red (t_RG = red - phase), at the time-only
+    cost (1 - gamma) t_RG; during green the jump is zero; a departure needs
+    green; engine torque at standstill forbids the step."""
+    p = P.toy_problem(seed=7, n_stages=3, with_light=True)
+    p = p.replace(cycle=np.array([20.0]), red=np.array([8.0]), offset=np.array([3.0]), light_model=2,
+                  n_te=2, te_lo=0.0, te_hi=150.0, n_tm=2, tm_lo=-60.0, tm_hi=60.0)
+    op = O.make(p)
+    k = 1  # the light node
+    # red: phase (t - 3) mod 20 = 2 s at t = 5 s -> 6 s of red left
+    r = O.model_step(op, k, 0.0, 0.55, 5.0, 0.0, -60.0, 0)
+    assert r is not None
+    assert r["v1"] == 0.0 and r["soc1"] == 0.55 and r["t1"] == pytest.approx(11.0, abs=1e-12)
+    assert r["dt"] == 0.0 and r["wait"] == pytest.approx(6.0, abs=1e-12)
+    assert r["cost"] == pytest.approx((1.0 - p.gamma) * 6.0, rel=1e-12)
+    assert O.model_step(op, k, 0.0, 0.55, 5.0, 150.0, 60.0, 0) is None   # departing during red
+    assert O.model_step(op, k, 0.0, 0.55, 5.0, 150.0, -60.0, 1) is None  # engine torque at standstill
+    # green: phase 10 s at t = 13 s -> the jump takes no time and costs nothing
+    g = O.model_step(op, k, 0.0, 0.55, 13.0, 0.0, -60.0, 0)
+    assert g is not None and g["t1"] == 13.0 and g["cost"] == 0.0 and g["v1"] == 0.0
+    dep = O.model_step(op, k, 0.0, 0.55, 13.0, 150.0, 60.0, 0)
+    assert dep is not None and dep["v1"] > 0.0 and dep["wait"] == 0.0
+    # away from a light node the default stopping rule applies
+    assert O.model_step(op, 0, 0.0, 0.55, 5.0, 0.0, -60.0, 0) is None
+
+
+def test_literal_standstill_without_lights_is_the_default():
+    p = small(seed=28)
+    p = p.replace(light_stage=np.zeros(0, np.int32), cycle=np.zeros(0), red=np.zeros(0), offset=np.zeros(0))
+    _, V0, pi0 = solve_nominal(p)
+    _, V2, pi2 = solve_nominal(p.replace(light_model=2))
+    assert all_equal(V0, V2) and all_equal(pi0, pi2)
+
+
+@pytest.mark.parametrize("cfg", [dict(seed=12, N=3, x0=(3.0, 0.60, 0.0), spat=(10.0, 5.0, 5.0)),
+                                 dict(seed=12, N=3, x0=(2.0, 0.60, 0.0), spat=(10.0, 5.0, 0.0)),
+                                 dict(seed=13, N=3, x0=(3.0, 0.60, 0.0), spat=(10.0, 5.0, 0.0)),
+                                 dict(seed=8, N=3, x0=(6.0, 0.55, 0.0))])
+def test_literal_standstill_bruteforce(cfg):
+    p = P.toy_problem(seed=cfg["seed"], n_stages=cfg["N"], with_light=True)
+    p = p.replace(x0=cfg["x0"], light_model=2)
+    if "spat" in cfg:
+        c, r, o = cfg["spat"]
+        p = p.replace(cycle=np.array([c]), red=np.array([r]), offset=np.array([o]))
+    grids = exact_grids(p, p.x0)
+    op = O.make(p, grids=grids)
+    Vs, _, _ = O.solve(op)
+    best, arg, _ = brute_force(op, p.x0, op.n_controls, p.n_stages)
+    assert np.isfinite(best)
+    assert Vs[0][0, 0, 0] == pytest.approx(best, rel=1e-12, abs=0)
+
+
+def test_literal_standstill_is_used():
+    """With red during [0, 5) s and a slow start the optimum stops at the line
+    (at 10 s, red again) and takes the standstill step to the end of red; the
+    default reading instead waits at the line and departs from it, cheaper
+    because it keeps the distance step for accelerating."""
+    p = P.toy_problem(seed=12, n_stages=3, with_light=True).replace(
+        x0=(2.0, 0.60, 0.0), light_model=2, cycle=np.array([10.0]), red=np.array([5.0]), offset=np.array([0.0]))
+    grids = exact_grids(p, p.x0)
+    op = O.make(p, grids=grids)
+    best, arg, _ = brute_force(op, p.x0, op.n_controls, p.n_stages)
+    x = np.array(p.x0, np.float64)
+    used = False
+    for k, u in enumerate(arg):
+        te, tm, b = op.decode(u)
+        r = O.model_step(op, k, x[0], x[1], x[2], te, tm, b)
+        if k == 1 and x[0] == 0.0 and r["v1"] == 0.0 and r["wait"] > 0.0:
+            used = True
+        x = np.array([r["v1"], r["soc1"], r["t1"]])
+    assert used
+    default = p.replace(light_model=0)
+    op0 = O.make(default, grids=exact_grids(default, default.x0))
+    best0, _, _ = brute_force(op0, default.x0, op0.n_controls, default.n_stages)
+    assert best0 < best
