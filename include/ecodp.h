@@ -92,9 +92,15 @@ typedef struct dp_problem_desc {
     const double *cycle, *red, *offset; /* [n_lights] s; red iff ((t - offset) mod cycle) < red */
     /* Paper variants; 0 selects the default reading. */
     int32_t light_model;  /* 0: an arrival at a light node with v' > 0 is checked at its continuous
-                             time; 1: the green indicator sampled on the time grid (Sec. III, Eq. 8):
+                             time, and a vehicle standing at the line waits for green;
+                             1: the green indicator sampled on the time grid (Sec. III, Eq. 8):
                              at a light node every state with v > 0 at a red time node is
-                             infeasible, and arrivals are not checked otherwise */
+                             infeasible, and arrivals are not checked otherwise;
+                             2: the literal standstill step of Eq. 5c: standing at a light node,
+                             a control without forward acceleration and with T_eng = 0 makes the
+                             distance step at zero speed while the clock jumps to the end of red
+                             (zero time during green), at the cost (1 - gamma) t_RG; a departure
+                             needs green */
     int32_t torque_limits; /* 0: the torque grids are the limits; 1: speed-dependent limits
                               (Eq. 7e, 7f) at the stage-start crank speed w = v gear / r_wheel */
     double te_max_coef[3]; /* torque_limits = 1: T_eng <= c0 + c1 w + c2 w^2 (Nm, w in rad/s) */

@@ -162,8 +162,8 @@ dp_status validate(const dp_problem_desc *d)
     for (int q = 0; q < d->n_stages; ++q)
         if (!std::isfinite(d->grade[q]) || std::fabs(d->grade[q]) > 1.0)
             return fail(DP_ERR_INVALID_ARG, "grade must be finite with |grade| <= 1");
-    if (d->light_model != 0 && d->light_model != 1)
-        return fail(DP_ERR_INVALID_ARG, "light_model must be 0 or 1");
+    if (d->light_model < 0 || d->light_model > 2)
+        return fail(DP_ERR_INVALID_ARG, "light_model must be 0, 1 or 2");
     if (d->torque_limits != 0 && d->torque_limits != 1)
         return fail(DP_ERR_INVALID_ARG, "torque_limits must be 0 or 1");
     if (d->torque_limits &&

@@ -105,6 +105,10 @@ __device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, c
         const float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
         red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
     }
+    // literal Eq. 5c: departing from the line needs green (no folded wait);
+    // the zero-speed step (v' = 0) lands at the end of red
+    if (P.light_model == 2 && si.wait_row && wait > 0.f && C.v1 > 0.f)
+        red = true;
     // a lower corner past the grid reads the padding column n_t; the upper
     // corner is the next column, still inside the row (ld_t >= n_t + 2)
     const int ta = red ? P.n_t : min(t0, P.n_t);

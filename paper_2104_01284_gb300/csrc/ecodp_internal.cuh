@@ -182,6 +182,19 @@ __device__ __forceinline__ bool speed_step(const DevParams &P, float v, float F_
     return true;
 }
 
+// The literal standstill step of Eq. 5c (light_model 2): from v = 0 at a
+// light node, a total torque T and brake b without forward acceleration (the
+// acceleration within the comfort limits and v'^2 = 2 ds a <= 0, the same
+// arithmetic as speed_step at v = 0) make the distance step at zero speed.
+__device__ __forceinline__ bool standstill_class(const DevParams &P, float F_road, float T, int b)
+{
+    float F_tr = __fsub_rn(__fmul_rn(T, P.ratio), b ? P.brake_force : 0.f);
+    float a = __fdiv_rn(__fsub_rn(F_tr, F_road), P.mass);
+    if (a < P.a_min || a > P.a_max)
+        return false;
+    return !(__fadd_rn(0.f, __fmul_rn(__fmul_rn(2.f, P.ds), a)) > 0.f);
+}
+
 // Fuel rate (g/s) of the engine at speed w (rad/s) and torque Te (Nm).
 __device__ __forceinline__ float fuel_rate(const DevParams &P, float w, float Te)
 {

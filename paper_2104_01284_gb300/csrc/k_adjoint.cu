@@ -33,12 +33,30 @@ __device__ bool step_grad(const DevParams &P, const StageTables &tb, int k, floa
     const float cos_th = __fdiv_rn(1.f, sq);
     const float F_road = road_load(P, v, __fdiv_rn(p, sq), cos_th);
     const int nl = tb.light_of_node[k + 1];
+    const int lk = tb.light_of_node[k];
+    if (P.light_model == 2 && lk >= 0 && v == 0.f) {
+        // literal Eq. 5c at the line: the zero-speed step has no theta
+        // dependence (v' = 0, SoC kept, time jump to the end of red)
+        const float ph = phase_pos(t, tb.offset[lk], tb.cycle[lk]);
+        const float wait = ph < tb.red[lk] ? __fsub_rn(tb.red[lk], ph) : 0.f;
+        if (standstill_class(P, F_road, T, b)) {
+            if (Te != 0.f || !torque_allowed(P, 0.f, Te, Tm))
+                return false;
+            for (int q = 0; q < 5; ++q)
+                o.dv1[q] = o.dxi1[q] = o.dt1[q] = o.dcost[q] = 0.f;
+            o.v1 = 0.f;
+            o.xi1 = xi;
+            o.t1 = __fadd_rn(t, wait);
+            return true;
+        }
+        if (wait > 0.f)
+            return false;
+    }
     float v1, dt;
     if (!speed_step(P, v, F_road, T, b, nl >= 0, v1, dt))
         return false;
     float wait = 0.f;
-    const int lk = tb.light_of_node[k];
-    if (lk >= 0 && v == 0.f) {
+    if (P.light_model != 2 && lk >= 0 && v == 0.f) {
         const float ph = phase_pos(t, tb.offset[lk], tb.cycle[lk]);
         if (ph < tb.red[lk])
             wait = __fsub_rn(tb.red[lk], ph);

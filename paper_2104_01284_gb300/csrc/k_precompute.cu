@@ -190,6 +190,8 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     const float w = __fmul_rn(v, P.ratio);
     const float one_m_gamma = __fsub_rn(1.f, P.gamma);
 
+    // standing at a light node under the literal Eq. 5c (light_model 2)
+    const bool stand = P.light_model == 2 && v == 0.f && tb.light_of_node[k] >= 0;
     const size_t row = (size_t)k * P.n_v + i;
     ClassRec *cls_row = sc.cls + row * P.n_cls;
     ClassEntry *ent_row = sc.ent + row * P.n_cls;
@@ -204,6 +206,13 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
             __fadd_rn(node_val(P.te_lo, P.te_span, ie0, P.n_te), node_val(P.tm_lo, P.tm_span, im0, P.n_tm));
         ClassRec rec = {};
         float v1 = 0.f, dt = 0.f;
+        if (stand && standstill_class(P, F_road, T, b)) {
+            // zero-speed step: v' = 0 (speed row 0), no driving time; the
+            // time jump to the end of red is taken per time node by the tile
+            rec.ok = 1;
+            cls_row[c] = rec;
+            continue;
+        }
         bool ok = speed_step(P, v, F_road, T, b, next_light, v1, dt);
         if (ok) {
             float qv = __fdiv_rn(__fsub_rn(v1, P.v_lo), P.h_v);
@@ -242,7 +251,9 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         float I;
         const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
         const float Te = node_val(P.te_lo, P.te_span, ie, P.n_te);
-        if (C.ok && torque_allowed(P, w, Te, Tm) && battery_current(P, w, Tm, I)) {
+        // the zero-speed step has the engine off (start-stop)
+        const bool engine_ok = !(stand && C.v1 == 0.f && C.dt == 0.f) || Te == 0.f;
+        if (C.ok && engine_ok && torque_allowed(P, w, Te, Tm) && battery_current(P, w, Tm, I)) {
             const float dxi = __fdiv_rn(__fmul_rn(C.dt, I), P.cap);
             snap_split(__fdiv_rn(-dxi, P.h_xi), r.d, r.f);
             const float mf = fuel_rate(P, w, Te);

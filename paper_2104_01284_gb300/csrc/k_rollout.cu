@@ -71,12 +71,32 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
     const float sq = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(p, p)));
     const float F_road = road_load(P, v, __fdiv_rn(p, sq), __fdiv_rn(1.f, sq));
     const int nl = tb.light_of_node[k + 1];
+    const int lk = tb.light_of_node[k];
+    const float one_m_gamma = __fsub_rn(1.f, P.gamma);
+    if (P.light_model == 2 && lk >= 0 && v == 0.f) {
+        // literal Eq. 5c at the line: the zero-speed step (engine off) jumps to
+        // the end of red; a departure needs green
+        const float ph = phase_pos(t, tb.offset[lk], tb.cycle[lk]);
+        const float wait = ph < tb.red[lk] ? __fsub_rn(tb.red[lk], ph) : 0.f;
+        if (standstill_class(P, F_road, __fadd_rn(Te, Tm), b)) {
+            if (Te != 0.f || !torque_allowed(P, 0.f, Te, Tm))
+                return false;
+            s.v1 = 0.f;
+            s.xi1 = xi;
+            s.dt = 0.f;
+            s.wait = wait;
+            s.mf = 0.f;
+            s.cost = __fmul_rn(one_m_gamma, wait);
+            return true;
+        }
+        if (wait > 0.f)
+            return false;
+    }
     float v1, dt;
     if (!speed_step(P, v, F_road, __fadd_rn(Te, Tm), b, nl >= 0, v1, dt))
         return false;
     float wait = 0.f;
-    const int lk = tb.light_of_node[k];
-    if (lk >= 0 && v == 0.f) {
+    if (P.light_model != 2 && lk >= 0 && v == 0.f) {
         float ph = phase_pos(t, tb.offset[lk], tb.cycle[lk]);
         if (ph < tb.red[lk])
             wait = __fsub_rn(tb.red[lk], ph);
@@ -92,7 +112,6 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
     if (!battery_current(P, w, Tm, I))
         return false;
     const float mf = fuel_rate(P, w, Te);
-    const float one_m_gamma = __fsub_rn(1.f, P.gamma);
     s.v1 = v1;
     s.xi1 = __fsub_rn(xi, __fdiv_rn(__fmul_rn(dt, I), P.cap));
     s.dt = dt;

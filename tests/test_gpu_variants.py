@@ -1,6 +1,7 @@
 """GPU parity of the paper variants with the FP64 oracle, through the C ABI
-(needs a GB300): speed-dependent torque limits (Eq. 7e, 7f) and the green
-indicator sampled on the time grid (Sec. III, Eq. 8), alone and together;
+(needs a GB300): speed-dependent torque limits (Eq. 7e, 7f), the green
+indicator sampled on the time grid (Sec. III, Eq. 8), alone and together, and
+the literal standstill step of Eq. 5c;
 stage-local and end-to-end with the acceptance criteria of tests/_parity.py,
 tiled and direct kernels bit-identical, and variant instances inside a batch
 equal to their single solves."""
@@ -21,6 +22,7 @@ VARIANTS = {
     "limits": lambda: reduced(seed=51).replace(**LIMITS),
     "sampled": lambda: reduced(seed=52).replace(light_model=1),
     "both": lambda: reduced(seed=53, n_te=7, n_tm=9).replace(light_model=1, **LIMITS),
+    "literal": lambda: reduced(seed=55).replace(light_model=2),
 }
 
 
