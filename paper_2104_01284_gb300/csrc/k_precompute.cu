@@ -264,15 +264,22 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     }
     __syncthreads();
 
-    // 3. compact the feasible classes; per class the lower envelope of each
-    // SoC-shift bucket d in {-2, -1, 0, 1}, then every control of any other
-    // shift (rare: one SoC step is far larger than a step's charge change)
+    // 3. the lower envelope of every (class, SoC-shift bucket d in
+    // {-2, -1, 0, 1}) pair, one pair per thread (members are disjoint)
+    for (int task = threadIdx.x; task < P.n_cls * 4; task += blockDim.x) {
+        const int c = task >> 2, bucket = task & 3;
+        bucket_envelope(P, class_members(P, c), c % P.n_b, bucket - 2, s_ctrl);
+    }
+    __syncthreads();
+
+    // 4. compact the feasible classes: the envelope lines of each bucket, then
+    // every control of any other shift (rare: one SoC step is far larger than
+    // a step's charge change)
     int ent_carry = 0, spl_carry = 0, feas_carry = 0;
     for (int c0 = 0; c0 < P.n_cls; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
         Members mem = {};
         int nspl = 0, nfeas = 0;
-        int nb[4] = {0, 0, 0, 0};
         if (c < P.n_cls) {
             mem = class_members(P, c);
             const int b = c % P.n_b;
@@ -280,15 +287,11 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
                 const CtrlRec r = s_ctrl[(ie * P.n_tm + member_im(mem, ie)) * P.n_b + b];
                 if (r.ok) {
                     ++nfeas;
-                    if (r.d < -2 || r.d > 1)
-                        ++nspl;
+                    ++nspl;
+                    if (r.d >= -2 && r.d <= 1 && r.ok != 2)
+                        --nspl;  // in a bucket but not on its envelope
                 }
             }
-            if (nfeas > 0)
-                for (int bucket = 0; bucket < 4; ++bucket) {
-                    nb[bucket] = bucket_envelope(P, mem, b, bucket - 2, s_ctrl);
-                    nspl += nb[bucket];
-                }
         }
         const int feas = nfeas > 0 ? 1 : 0;
         int ent_tot, spl_tot, feas_tot;

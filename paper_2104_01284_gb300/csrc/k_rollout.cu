@@ -121,7 +121,7 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
     return true;
 }
 
-constexpr int ROLL_THREADS = 512;
+constexpr int ROLL_THREADS = 1024;
 
 // The rollout of one problem by the whole CTA over stages [k_begin, k_end).
 // A later segment continues from the state, fuel, cost and fail stage the
@@ -136,7 +136,8 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     __shared__ double s_t, s_fuel, s_J;
     __shared__ float red_F[ROLL_THREADS / 32];
     __shared__ int red_u[ROLL_THREADS / 32];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_win;
+    __shared__ Step s_step;
     if (threadIdx.x == 0)
         P = *dP;
     __syncthreads();
@@ -174,6 +175,7 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
         const float *Vn = view.at(k + 1);
         float bF = __int_as_float(0x7f800000);
         int bu = INT_MAX;
+        Step bs = {};
         for (int u = threadIdx.x; u < P.n_u; u += blockDim.x) {
             Step s;
             if (!model_step(P, tb, k, v, xi, t, u, s))
@@ -182,8 +184,10 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
             if (F < V_FEAS_MAX && (F < bF || (F == bF && u < bu))) {
                 bF = F;
                 bu = u;
+                bs = s;
             }
         }
+        const int my_u = bu;
         // block argmin on (F, u)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -207,11 +211,18 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
                     bu = red_u[w];
                 }
             }
+            s_win = bu;
+        }
+        __syncthreads();
+        if (my_u == s_win && my_u != INT_MAX)
+            s_step = bs;  // the winning thread hands over its step record
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bu = s_win;
             if (bu == INT_MAX) {
                 s_fail = k;
             } else {
-                Step s;
-                model_step(P, tb, k, v, xi, t, bu, s);
+                const Step s = s_step;
                 out_u[k] = bu;
                 o_dt[k] = s.dt;
                 o_wait[k] = s.wait;
