@@ -54,9 +54,12 @@ __device__ __forceinline__ int upper_bound_idx(const T *a, int n, T x)  // first
     return lo;
 }
 
-template <int R>
-__global__ void __launch_bounds__(TLANES, 4) bellman_persistent(const DevParams *__restrict__ params,
-                                                               const BatchInst *__restrict__ inst, BatchSched S)
+// MINB: resident CTAs per SM the register budget is sized for (4: 128
+// registers per thread, 5: 96, 6: 80); the launch picks the instance for the
+// requested residency.
+template <int R, int MINB>
+__global__ void __launch_bounds__(TLANES, MINB) bellman_persistent(const DevParams *__restrict__ params,
+                                                                  const BatchInst *__restrict__ inst, BatchSched S)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevParams P;
@@ -118,30 +121,61 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_persistent(const DevParams 
     }
 }
 
-template <int R>
-cudaError_t max_ctas_r(size_t smem, int *per_sm)
+template <int R, int MINB>
+cudaError_t max_ctas_rm(size_t smem, int *per_sm)
 {
     cudaError_t err =
-        cudaFuncSetAttribute(bellman_persistent<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(bellman_persistent<R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess)
         return err;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bellman_persistent<R>, TLANES, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, bellman_persistent<R, MINB>, TLANES, smem);
     if (err != cudaSuccess)
         return err;
+    if (*per_sm > MINB && MINB < 6)  // a larger budget instance is only used up to its own residency
+        *per_sm = MINB;
     return *per_sm < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 
+// The most CTAs per SM any instance of rows-per-lane R reaches.
 template <int R>
-cudaError_t launch_persistent_r(const DevParams *params, const BatchInst *inst, const BatchSched &S, size_t smem,
-                                int ctas_per_sm, int num_sms, cudaStream_t s)
+int max_ctas_r(size_t smem)
 {
-    int per_sm = 0;
-    cudaError_t err = max_ctas_r<R>(smem, &per_sm);
+    int best = 0;
+    const int budgets[3] = {4, 5, 6};
+    for (int mb : budgets) {
+        int n = 0;
+        cudaError_t e = cudaSuccess;
+        if (R == 8 && mb == 4)
+            e = max_ctas_rm<8, 4>(smem, &n);
+        else if (R == 8 && mb == 5)
+            e = max_ctas_rm<8, 5>(smem, &n);
+        else if (R == 4 && mb == 4)
+            e = max_ctas_rm<4, 4>(smem, &n);
+        else if (R == 4 && mb == 5)
+            e = max_ctas_rm<4, 5>(smem, &n);
+        else if (R == 4 && mb == 6)
+            e = max_ctas_rm<4, 6>(smem, &n);
+        else
+            continue;
+        if (e != cudaSuccess)
+            cudaGetLastError();
+        else
+            best = n > best ? n : best;
+    }
+    return best;
+}
+
+template <int R, int MINB>
+cudaError_t launch_rm(const DevParams *params, const BatchInst *inst, const BatchSched &S, size_t smem, int per_sm,
+                      int num_sms, cudaStream_t s)
+{
+    int fit = 0;
+    cudaError_t err = max_ctas_rm<R, MINB>(smem, &fit);
     if (err != cudaSuccess)
         return err;
-    if (ctas_per_sm > 0 && ctas_per_sm < per_sm)
-        per_sm = ctas_per_sm;
-    bellman_persistent<R><<<num_sms * per_sm, TLANES, smem, s>>>(params, inst, S);
+    if (per_sm > fit)
+        return cudaErrorInvalidConfiguration;
+    bellman_persistent<R, MINB><<<num_sms * per_sm, TLANES, smem, s>>>(params, inst, S);
     return cudaGetLastError();
 }
 
@@ -160,9 +194,7 @@ int persistent_chunks_per_row(int rows_per_lane, int n_xi, int n_t)
 int persistent_max_ctas_per_sm(int rows_per_lane, int max_n_cls, int max_n_u)
 {
     const size_t smem = persistent_smem_bytes(rows_per_lane, max_n_cls, max_n_u);
-    int per_sm = 0;
-    const cudaError_t err = rows_per_lane == 4 ? max_ctas_r<4>(smem, &per_sm) : max_ctas_r<8>(smem, &per_sm);
-    return err == cudaSuccess ? per_sm : 0;
+    return rows_per_lane == 4 ? max_ctas_r<4>(smem) : max_ctas_r<8>(smem);
 }
 
 cudaError_t launch_persistent(const DevParams *params, const BatchInst *inst, const BatchSched &S, int rows_per_lane,
@@ -176,9 +208,22 @@ cudaError_t launch_persistent(const DevParams *params, const BatchInst *inst, co
     if (err != cudaSuccess)
         return err;
     const size_t smem = persistent_smem_bytes(rows_per_lane, max_n_cls, max_n_u);
-    if (rows_per_lane == 4)
-        return launch_persistent_r<4>(params, inst, S, smem, ctas_per_sm, num_sms, s);
-    return launch_persistent_r<8>(params, inst, S, smem, ctas_per_sm, num_sms, s);
+    int per_sm = ctas_per_sm;
+    if (per_sm <= 0)
+        per_sm = persistent_max_ctas_per_sm(rows_per_lane, max_n_cls, max_n_u);
+    if (per_sm < 1)
+        return cudaErrorInvalidConfiguration;
+    // the smallest register budget that holds the requested residency
+    if (rows_per_lane == 4) {
+        if (per_sm <= 4)
+            return launch_rm<4, 4>(params, inst, S, smem, per_sm, num_sms, s);
+        if (per_sm == 5)
+            return launch_rm<4, 5>(params, inst, S, smem, per_sm, num_sms, s);
+        return launch_rm<4, 6>(params, inst, S, smem, per_sm, num_sms, s);
+    }
+    if (per_sm <= 4)
+        return launch_rm<8, 4>(params, inst, S, smem, per_sm, num_sms, s);
+    return launch_rm<8, 5>(params, inst, S, smem, per_sm, num_sms, s);
 }
 
 }  // namespace ecodp

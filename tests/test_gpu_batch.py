@@ -59,7 +59,7 @@ def same_traj(a, b):
         assert a["fuel_g"] == b["fuel_g"] and a["time_s"] == b["time_s"] and a["J"] == b["J"]
 
 
-@pytest.mark.parametrize("R,c", [(8, 0), (4, 0), (8, 1), (4, 2)])
+@pytest.mark.parametrize("R,c", [(8, 0), (4, 0), (8, 1), (4, 2), (8, 5), (4, 6)])
 def test_batch_bit_identical_to_alone(mods, small, R, c):
     probs, alone = small
     with mods.EcoDPBatch(probs, rows_per_lane=R, ctas_per_sm=c) as bt:
