@@ -302,6 +302,36 @@ def bench_serving(dev, seconds):
             "one_at_a_time": single, "deadline_s": 1.0, "slot_stats": stats}
 
 
+def bench_paper_grid(dev, stream, reps=20):
+    """The grid of the paper's Table I (20 steps, 35 x 26 x 40 states, 23 x 30
+    torques = 5.0e8 nominal evaluations per solve), solved by the
+    single-problem path: median and p99 of `reps` graph-launched solves."""
+    import torch
+
+    from paper_2104_01284_gb300 import problems as P
+    from paper_2104_01284_gb300.solver import EcoDP
+    p = P.paper_table1()
+    dp = EcoDP(p, device=dev, stream=stream)
+    for _ in range(3):
+        dp.solve(stream)
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dp.solve(stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    dp.close()
+    ms = statistics.median(times)
+    return {"workload": "grid of the paper's Table I: 20 stages x 35x26x40 states x 23x30 torques (seed 5)",
+            "evals_per_solve": p.evals_per_solve, "ms_per_solve_median": ms,
+            "ms_per_solve_p99": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
+            "nominal_evals_per_s": p.evals_per_solve / (ms / 1e3),
+            "paper_context_ms": {"rtx2080_parallel_mean": 98, "cpu_serial_mean": 1600}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -410,6 +440,7 @@ def run_ours(args):
     adjoint = {"ms_per_call": 1e3 * (time.perf_counter() - t0) / 3, "J0": J0,
                "dJ_dtheta": dict(zip(("mass", "cda", "crr", "r0", "fuel_scale"), map(float, grad)))}
 
+    paper_grid = bench_paper_grid(dev, stream)
     batched = bench_batched(args.batch, dev, stream) if args.batch > 0 else None
     serving = bench_serving(dev, args.serve_seconds) if args.serve_seconds > 0 else None
 
@@ -423,7 +454,7 @@ def run_ours(args):
         "ms_per_solve_p99": float(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))]),
         "rollout": {"fuel_g": traj["fuel_g"], "time_s": traj["time_s"], "J": traj["J"]},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks, "adjoint": adjoint, "batched": batched,
+        "clocks": clocks, "adjoint": adjoint, "paper_grid": paper_grid, "batched": batched,
         "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

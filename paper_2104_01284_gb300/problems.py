@@ -40,6 +40,7 @@ __all__ = [
     "config3_batch",
     "config3_small",
     "config4_fleet",
+    "paper_table1",
     "toy_problem",
     "uniform_nodes",
     "synthetic_value_field",
@@ -355,6 +356,25 @@ def horizon_problem(fuel: np.ndarray, route, start_node: int, t0: float,
         n_brake=2, fuel_coef=np.array(fuel, copy=True),
         light_stage=rel[keep].astype(np.int32), cycle=cyc[keep], red=red[keep],
         offset=off[keep])
+
+
+def paper_table1(seed: int = 5) -> Problem:
+    """The grid of the paper's timing study (Sec. V, Table I): a 200 m
+    horizon of 20 steps of 10 m with t_f = 80 s; 35 speeds x 26 SoC points x
+    40 time points; 23 engine x 30 BSG torques (no brake flag: the paper's
+    controls are the two torques).  Seeded stand-in for its routes: grade
+    U(+-3 %), one light in the window with the SPaT of config 1.  Draw order:
+    fuel coefficients, grade, light."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fuel = _draw_fuel(rng)
+    grade = rng.uniform(-0.03, 0.03, size=20)
+    nodes, cyc, red, off = _draw_lights(rng, 1, 2, 18)
+    return Problem(
+        name=f"paper-table1-s{seed}", n_stages=20, ds=10.0, grade=grade,
+        v_lo=0.0, v_hi=25.0, n_v=35, soc_lo=0.30, soc_hi=0.80, n_soc=26,
+        t_lo=0.0, t_hi=80.0, n_t=40,
+        te_lo=0.0, te_hi=200.0, n_te=23, tm_lo=-100.0, tm_hi=100.0, n_tm=30,
+        n_brake=1, fuel_coef=fuel, light_stage=nodes, cycle=cyc, red=red, offset=off)
 
 
 def toy_problem(seed: int = 7, n_stages: int = 3, with_light: bool = True) -> Problem:

@@ -62,6 +62,8 @@ PROBLEMS = {
     "c0": lambda: P.config0(),
     "reduced": lambda: reduced(),
     "reduced_s2": lambda: reduced(seed=32, n_soc=11, n_t=33, n_te=7, n_tm=9),  # unequal torque steps
+    # the grid of the paper's Table I: 690 controls, one torque class each
+    "paper_grid": lambda: P.paper_table1(),
 }
 
 
@@ -110,7 +112,7 @@ def feasible_start(p, V0, V0lo, V0hi):
     return (float(vg[i]), float(sg[j]), float(tg[l]))
 
 
-@pytest.mark.parametrize("name", ["c0", "reduced"])
+@pytest.mark.parametrize("name", ["c0", "reduced", "paper_grid"])
 def test_end_to_end_parity_and_rollout(gpu, name):
     p = PROBLEMS[name]()
     op = O.make(p)
