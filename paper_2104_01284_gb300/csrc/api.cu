@@ -78,7 +78,8 @@ struct dp_problem {
     bool use_graph = true;
 
     StageTables tables() const { return StageTables{d_grade, d_lon, d_cyc, d_red, d_off}; }
-    StageScratch scratch() const { return StageScratch{d_cls, d_ent, d_rowcnt, d_spl, d_stats}; }
+    unsigned long long *d_part = nullptr;  // per-state minima of the class-split Bellman launch
+    StageScratch scratch() const { return StageScratch{d_cls, d_ent, d_rowcnt, d_spl, d_stats, d_part}; }
     // Value-function storage.  ckpt == 0: every stage k at d_V + k stage_elems.
     // ckpt = K >= 2: only stages 0, K, 2K, ... and N are kept (checkpoints,
     // in that order in d_V); the backward sweep writes the other stages to
@@ -579,12 +580,15 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, (size_t)5, &p->d_stats));
     TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_lam));
     TRY(dev_alloc_n(p, (size_t)8, &p->d_adj));
+    TRY(dev_alloc_n(p, p->pi_elems, &p->d_part));
     TRY(upload_tables(p, p->create_stream));
     auto cuda_try = [&](cudaError_t e, const char *what) -> dp_status {
         if (e != cudaSuccess)
             return fail(DP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
         return DP_OK;
     };
+    TRY(cuda_try(cudaMemsetAsync(p->d_part, 0xff, p->pi_elems * sizeof(unsigned long long), p->create_stream),
+                 "clear split minima"));
     // every padding cell holds the infeasible sentinel for the object's life
     TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
@@ -1020,7 +1024,7 @@ extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t 
                    (const float *)(tb_dev + offsetof(decltype(tbl), red)),
                    (const float *)(tb_dev + offsetof(decltype(tbl), off))};
     StageScratch sc{(ClassRec *)(base + ST_OFF_CLS), (ClassEntry *)(base + ST_OFF_ENT), (int *)(base + ST_OFF_ROWCNT),
-                    (SplitRec *)(base + ST_OFF_SPL), nullptr};
+                    (SplitRec *)(base + ST_OFF_SPL), nullptr, nullptr};
     if (P.ld_t > (int)STATIC_LD_T || (size_t)P.n_v * P.xi_rows * P.ld_t > STATIC_PAD_ELEMS)
         return fail(DP_ERR_INTERNAL, "static working memory layout too small");
     float *pad_in = (float *)(base + ST_OFF_PAD_IN);

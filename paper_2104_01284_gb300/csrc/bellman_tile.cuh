@@ -332,11 +332,26 @@ __host__ __device__ inline int chunks_per_row(int n_xi, int n_t)
 // are (cls, ent, spl) with n_ent feasible classes and n_spl controls.  All
 // TLANES threads of the CTA call it; it starts with a barrier so the shared
 // memory can be reused by the next tile.
-template <int R, bool NC>
+// Tile modes: the whole class list (TILE_FULL); a slice [e_begin, e_end) of
+// it whose per-state minimum, packed as (value bits << 32 | class), is
+// merged into `part` with atomicMin (TILE_SLICE: values are non-negative, so
+// their bit patterns order like the floats, and equal values keep the lower
+// class, the tie order below); or the join of the slices (TILE_JOIN: read and
+// reset `part`, then write J_k and recover the argmin exactly as TILE_FULL).
+constexpr int TILE_FULL = 0, TILE_SLICE = 1, TILE_JOIN = 2;
+
+__device__ __forceinline__ unsigned long long pack_min(float v, int e)
+{
+    const float z = __fadd_rn(v, 0.f);  // -0 -> +0
+    return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)e;
+}
+
+template <int R, bool NC, int MODE = TILE_FULL>
 __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, const ClassRec *g_cls,
                              const ClassEntry *g_ent, const SplitRec *g_spl, int n_ent, int n_spl, const float *Vn,
                              float *__restrict__ Vk, int16_t *__restrict__ pik, int i, int chunk,
-                             unsigned char *smem_raw, unsigned long long *stats)
+                             unsigned char *smem_raw, unsigned long long *stats, int e_begin = 0, int e_end = 0,
+                             unsigned long long *__restrict__ part = nullptr)
 {
     const int tid = threadIdx.x;
     const Layout L = layout<R>(P.n_cls, P.n_u);
@@ -396,7 +411,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         best[r] = __int_as_float(0x7f800000);
         bcls[r] = 0;
     }
-    for (int e = 0; e < n_ent; ++e) {
+    const int e_lo = MODE == TILE_SLICE ? e_begin : 0;
+    const int e_hi = MODE == TILE_SLICE ? min(e_end, n_ent) : (MODE == TILE_JOIN ? 0 : n_ent);
+    for (int e = e_lo; e < e_hi; ++e) {
         const ClassEntry E = s_ent[e];
         const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
         // window rows jb - 2 .. jb + R + 1; the outermost two only for the
@@ -455,6 +472,31 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             if (cls_min[r] < best[r]) {
                 best[r] = cls_min[r];
                 bcls[r] = e;
+            }
+        }
+    }
+
+    if (MODE == TILE_SLICE) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = jb + r;
+            if (f_ok && j < P.n_xi && best[r] < __int_as_float(0x7f800000))
+                atomicMin(part + ((size_t)i * P.n_xi + j) * P.n_t + l, pack_min(best[r], bcls[r]));
+        }
+        return;
+    }
+    if (MODE == TILE_JOIN) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = jb + r;
+            if (f_ok && j < P.n_xi) {
+                unsigned long long *q = part + ((size_t)i * P.n_xi + j) * P.n_t + l;
+                const unsigned long long w = *q;
+                *q = ~0ull;  // ready for the next stage
+                if (w != ~0ull) {
+                    best[r] = __uint_as_float((unsigned)(w >> 32));
+                    bcls[r] = (int)(unsigned)(w & 0xffffffffu);
+                }
             }
         }
     }

@@ -262,6 +262,9 @@ struct StageScratch {
     // (v, class) pairs, states whose minimum ties across classes, states
     // whose argmin was recovered, (v, u) pairs kept in the tables (envelopes)
     unsigned long long *stats;
+    // [n_v][n_soc][n_t] packed per-state minima of the class-split Bellman
+    // launch (all ones between stages); NULL: never split
+    unsigned long long *part;
 };
 
 // One instance of a batch (device-resident descriptor).

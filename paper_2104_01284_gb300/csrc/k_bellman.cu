@@ -3,7 +3,8 @@
 //   * bellman_direct: one thread per state, every control evaluated with its
 //     own reads of J_{k+1} (the layout of the paper's second kernel, Sec. IV);
 //   * bellman_tiled: one CTA per tile (speed row, 128 lanes) running the
-//     torque-class tile of bellman_tile.cuh.
+//     torque-class tile of bellman_tile.cuh; on grids whose tiles cannot fill
+//     the GPU, bellman_slice + bellman_join split each tile's classes.
 #include <cfloat>
 #include <climits>
 
@@ -84,6 +85,60 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_tiled(const DevParams *__re
                                  sc.stats);
 }
 
+// Class-split tiles for grids whose tiles cannot fill the GPU: blockIdx.z
+// picks one of gridDim.z slices of the row's class list; a join launch then
+// writes J_k and the argmin (TILE_SLICE / TILE_JOIN in bellman_tile.cuh).
+__global__ void __launch_bounds__(TLANES, 4) bellman_slice(const DevParams *__restrict__ dP, StageTables tb, int k,
+                                                          StageScratch sc, const float *__restrict__ Vn)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ DevParams P;
+    if (threadIdx.x == 0)
+        P = *dP;
+    __syncthreads();
+    const int i = blockIdx.y;
+    const size_t row = (size_t)k * P.n_v + i;
+    const int n_ent = sc.row_cnt[2 * row];
+    const int e0 = (int)((long long)n_ent * blockIdx.z / gridDim.z);
+    const int e1 = (int)((long long)n_ent * (blockIdx.z + 1) / gridDim.z);
+    if (e0 >= e1)
+        return;  // an empty slice (uniform over the CTA)
+    bellman_tile<R_SINGLE, true, TILE_SLICE>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
+                                             sc.spl + row * P.n_u, n_ent, sc.row_cnt[2 * row + 1], Vn, nullptr,
+                                             nullptr, i, blockIdx.x, smem_raw, nullptr, e0, e1, sc.part);
+}
+
+__global__ void __launch_bounds__(TLANES, 4) bellman_join(const DevParams *__restrict__ dP, StageTables tb, int k,
+                                                         StageScratch sc, const float *__restrict__ Vn,
+                                                         float *__restrict__ Vk, int16_t *__restrict__ pik)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ DevParams P;
+    if (threadIdx.x == 0)
+        P = *dP;
+    __syncthreads();
+    const int i = blockIdx.y;
+    const size_t row = (size_t)k * P.n_v + i;
+    bellman_tile<R_SINGLE, true, TILE_JOIN>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
+                                            sc.spl + row * P.n_u, sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn,
+                                            Vk, pik, i, blockIdx.x, smem_raw, sc.stats, 0, 0, sc.part);
+}
+
+// Class slices per tile: as many as keep the GPU's resident CTA slots (4 per
+// SM) filled, at most 8; 1 (no split) when the tiles alone fill the slots.
+int class_slices(int tiles)
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    const int s = (4 * sms) / (tiles > 0 ? tiles : 1);
+    return s < 1 ? 1 : (s > 8 ? 8 : s);
+}
+
 }  // namespace
 
 size_t bellman_smem_bytes(const DevParams &hP) { return layout<R_SINGLE>(hP.n_cls, hP.n_u).total; }
@@ -97,10 +152,26 @@ cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables
         return cudaGetLastError();
     }
     const size_t smem = bellman_smem_bytes(hP);
+    const int chunks = chunks_per_row<R_SINGLE>(hP.n_xi, hP.n_t);
+    const int slices = sc.part ? class_slices(chunks * hP.n_v) : 1;
+    if (slices > 1) {
+        cudaError_t err =
+            cudaFuncSetAttribute(bellman_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+        err = cudaFuncSetAttribute(bellman_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+        bellman_slice<<<dim3(chunks, hP.n_v, slices), TLANES, smem, s>>>(dP, tb, k, sc, Vnext);
+        err = cudaGetLastError();
+        if (err != cudaSuccess)
+            return err;
+        bellman_join<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
+        return cudaGetLastError();
+    }
     cudaError_t err = cudaFuncSetAttribute(bellman_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess)
         return err;
-    const int chunks = chunks_per_row<R_SINGLE>(hP.n_xi, hP.n_t);
     bellman_tiled<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
     return cudaGetLastError();
 }
