@@ -283,6 +283,7 @@ typedef struct dp_multi *dp_multi_t;
 typedef struct dp_multi_opts {
     int32_t rows_per_lane; /* SoC rows per lane of a Bellman tile: 4 or 8 (0 = 8) */
     int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent launch (0 = as many as fit) */
+    int32_t wait_limit_ms; /* bound of one dependency wait of the persistent launch (0 = 10000) */
 } dp_multi_opts;
 
 /* Validate descs[0..n-1] (the rules of dp_problem_create, instance by
@@ -325,6 +326,13 @@ dp_status dp_multi_profile(dp_multi_t m, void *stream, float ms[3]);
  * rows_per_lane, best[1] = ctas_per_sm; *best_ms (may be NULL) its time.
  * Synchronises; leaves the batch solved. */
 dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t best[2], float *best_ms);
+
+/* Test hook for the timeout path: raise instance b's per-stage completion
+ * target by one, so that every dependency wait on b's stages runs out
+ * (bounded by wait_limit_ms each) and the next synchronising call reports
+ * DP_ERR_TIMEOUT; the results of b are then meaningless.  dp_multi_set_config
+ * restores the target.  DP_ERR_INVALID_ARG for a bad index. */
+dp_status dp_multi_debug_stall(dp_multi_t m, int32_t b);
 
 /* out[0] instances, out[1] work items of the persistent launch, out[2] its
  * CTAs, out[3] rows_per_lane, out[4] CTAs per SM, out[5] nominal state x

@@ -40,6 +40,7 @@ struct dp_multi {
     int max_n = 0, max_n_u = 0, max_n_cls = 0;
     long long n_rows = 0, n_items = 0;
     int rows_per_lane = 8, ctas_per_sm = 0;
+    unsigned long long wait_limit_ns = 10ull * 1000 * 1000 * 1000;  // 10 s
     // rollout buffers
     double *d_x0 = nullptr, *d_out = nullptr;
     int *d_out_u = nullptr;
@@ -54,7 +55,7 @@ struct dp_multi {
 
     BatchSched sched() const
     {
-        return BatchSched{d_order, d_pref, d_start, d_m, max_n, n_items, d_queue, d_error};
+        return BatchSched{d_order, d_pref, d_start, d_m, max_n, n_items, d_queue, d_error, wait_limit_ns};
     }
 };
 
@@ -342,6 +343,10 @@ dp_status dp_multi_create(const dp_problem_desc *descs, int32_t n, const dp_mult
         TRY(cuda_try(launch_fill(I.V, I.stage_elems * (size_t)(I.N + 1), V_BIG, s), "fill V"));
     }
     TRY(cuda_try(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
+    if (opts && opts->wait_limit_ms < 0)
+        TRY(fail(DP_ERR_INVALID_ARG, "wait_limit_ms must be >= 0"));
+    if (opts && opts->wait_limit_ms > 0)
+        m->wait_limit_ns = (unsigned long long)opts->wait_limit_ms * 1000000ull;
     // build_schedule synchronises s, so the host staging vectors above outlive their copies
     TRY(set_config(m, opts ? opts->rows_per_lane : 0, opts ? opts->ctas_per_sm : 0));
 #undef TRY
@@ -471,6 +476,17 @@ dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t
     best[1] = c_best;
     if (best_ms)
         *best_ms = t_best;
+    return DP_OK;
+}
+
+dp_status dp_multi_debug_stall(dp_multi_t m, int32_t b)
+{
+    if (!m || b < 0 || b >= m->B)
+        return fail(DP_ERR_INVALID_ARG, "bad batch or instance");
+    BatchInst I = m->h_inst[b];
+    I.tiles += 1;  // a completion target that the instance's tiles never reach
+    DP_CUDA(cudaMemcpyAsync(m->d_inst + b, &I, sizeof I, cudaMemcpyHostToDevice, m->create_stream));
+    DP_CUDA(cudaStreamSynchronize(m->create_stream));
     return DP_OK;
 }
 

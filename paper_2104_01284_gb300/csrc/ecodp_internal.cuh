@@ -274,7 +274,7 @@ struct BatchInst {
     float *V;              // [N+1] padded stages
     int16_t *pi;           // [N] stages
     size_t stage_elems, pi_elems;
-    int N, chunks, tiles;  // lane chunks per speed row and tiles per stage of the batched kernel
+    int N, chunks, tiles;  // lane chunks per speed row; tiles per stage (the completion target of a stage)
     int pad;
     int *done;             // [N] completed tiles of each stage (stage k at done[k])
     long long row_off;     // first block of this instance in the batched precompute grid
@@ -329,6 +329,7 @@ struct BatchSched {
     long long n_items;
     unsigned long long *queue;  // next item (zero before the launch)
     int *error;                 // set to 1 when a dependency wait times out
+    unsigned long long wait_limit_ns;  // bound of one dependency wait
 };
 
 cudaError_t launch_terminal_batched(const DevParams *params, const BatchInst *inst, int n_inst, cudaStream_t s);

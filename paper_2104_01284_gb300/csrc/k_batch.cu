@@ -19,7 +19,6 @@ namespace {
 
 using namespace tile;
 
-constexpr unsigned long long WAIT_LIMIT_NS = 10ull * 1000 * 1000 * 1000;  // 10 s
 
 __device__ __forceinline__ int ld_acquire(const int *p)
 {
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(TLANES, MINB) bellman_persistent(const DevPara
             if (threadIdx.x == 0) {
                 const unsigned long long t0 = global_ns();
                 while (ld_acquire(I.done + k + 1) < I.tiles) {
-                    if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                    if (global_ns() - t0 > S.wait_limit_ns) {
                         atomicExch(S.error, 1);
                         break;
                     }

@@ -118,7 +118,7 @@ EXPORTED.append("dp_adjoint")
 
 
 class MultiOpts(C.Structure):
-    _fields_ = [("rows_per_lane", C.c_int32), ("ctas_per_sm", C.c_int32)]
+    _fields_ = [("rows_per_lane", C.c_int32), ("ctas_per_sm", C.c_int32), ("wait_limit_ms", C.c_int32)]
 
 
 dp_multi_create = _sig("dp_multi_create", C.POINTER(ProblemDesc), C.c_int32, C.POINTER(MultiOpts),
@@ -130,12 +130,13 @@ dp_multi_wait = _sig("dp_multi_wait", vp, vp)
 dp_multi_profile = _sig("dp_multi_profile", vp, vp, C.POINTER(C.c_float))
 dp_multi_autotune = _sig("dp_multi_autotune", vp, vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float))
 dp_multi_info = _sig("dp_multi_info", vp, C.POINTER(C.c_int64))
+dp_multi_debug_stall = _sig("dp_multi_debug_stall", vp, C.c_int32)
 dp_multi_get_value = _sig("dp_multi_get_value", vp, C.c_int32, C.c_int32, vp, C.c_int32, vp)
 dp_multi_get_policy = _sig("dp_multi_get_policy", vp, C.c_int32, C.c_int32, vp, C.c_int32, vp)
 dp_multi_rollout = _sig("dp_multi_rollout", vp, dbl_p, C.POINTER(Trajectory), vp)
 EXPORTED += ["dp_multi_create", "dp_multi_destroy", "dp_multi_set_config", "dp_multi_solve", "dp_multi_wait",
              "dp_multi_profile", "dp_multi_autotune", "dp_multi_info", "dp_multi_get_value", "dp_multi_get_policy",
-             "dp_multi_rollout"]
+             "dp_multi_rollout", "dp_multi_debug_stall"]
 
 # serving: continuous batching of receding-horizon re-solves
 dp_batch_create = _sig("dp_batch_create", C.c_int32, C.c_size_t, C.POINTER(Allocator), C.POINTER(vp))

@@ -284,7 +284,7 @@ class EcoDPBatch:
     """
 
     def __init__(self, probs, device=None, stream=None, rows_per_lane: int = 0, ctas_per_sm: int = 0,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, wait_limit_ms: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("EcoDPBatch needs a CUDA device; the solver has no CPU fallback")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -296,7 +296,7 @@ class EcoDPBatch:
             d, k = make_desc(p)
             descs[b] = d
             keep.append(k)
-        opts = N.MultiOpts(int(rows_per_lane), int(ctas_per_sm))
+        opts = N.MultiOpts(int(rows_per_lane), int(ctas_per_sm), int(wait_limit_ms))
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             N.check(N.dp_multi_create(descs, len(self.probs), C.byref(opts),
@@ -351,6 +351,11 @@ class EcoDPBatch:
             N.check(N.dp_multi_autotune(self.h, _stream_handle(stream), int(repeats), best, C.byref(t)),
                     "dp_multi_autotune")
         return dict(rows_per_lane=best[0], ctas_per_sm=best[1], ms=t.value)
+
+    def debug_stall(self, b: int):
+        """Test hook: make every dependency wait on instance b run out."""
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_debug_stall(self.h, int(b)), "dp_multi_debug_stall")
 
     def info(self):
         out = (C.c_int64 * 8)()

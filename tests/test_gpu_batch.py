@@ -145,3 +145,26 @@ def test_paper_scale_batch_slice_matches_alone(mods):
                 assert np.array_equal(bits(bt.value(b, k).cpu().numpy()), bits(dp.value(k).cpu().numpy()))
                 assert torch.equal(bt.policy(b, k), dp.policy(k))
             dp.close()
+
+
+def test_dependency_wait_timeout_is_reported(mods):
+    """A dependency that nothing completes (test hook): every wait on the
+    stalled instance gives up after its 20 ms bound, the launch ends, the
+    next synchronising call reports DP_ERR_TIMEOUT, and the batch stays
+    usable (reconfiguring restores the schedule; results equal single solves)."""
+    import paper_2104_01284_gb300.native as N
+    probs = P.config3_small(seed=36, n_instances=3)
+    with mods.EcoDPBatch(probs, wait_limit_ms=20) as bt:
+        bt.debug_stall(1)
+        bt.solve()
+        with pytest.raises(N.DPError) as e:
+            bt.wait()
+        assert e.value.status == N.DP_ERR_TIMEOUT
+        bt.set_config(8, 0)
+        bt.solve()
+        bt.wait()
+        for b, p in enumerate(probs):
+            dp = mods.EcoDP(p)
+            dp.solve()
+            assert torch.equal(bt.value(b, 0), dp.value(0))
+            dp.close()
