@@ -154,6 +154,23 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in `seconds`
+    (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
@@ -377,12 +394,8 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1))
     barrier()
     clocks = sampler.stop()
-    total_ms = sum(times)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * p.evals_per_solve * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dev)
+    value = job_rate(p.evals_per_solve * args.steps, world, total_ms / 1e3)
 
     # per-kernel breakdown (direct launches, CUDA events on the launching stream)
     profs = [dp.profile_sweep(stream) for _ in range(3)]
@@ -423,13 +436,10 @@ def run_ours(args):
         dp.solve(stream)
         dp.rollout(stream=stream)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * p.evals_per_solve * args.steps / float(te.item()), "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e = {"value": job_rate(p.evals_per_solve * args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(stats["h2d_update_bytes"]), "d2h_bytes_per_step": int(stats["d2h_rollout_bytes"]),
-           "ms_per_step": 1e3 * float(te.item()) / args.steps}
+           "ms_per_step": 1e3 * e2e_s / args.steps}
 
     # adjoint dJ*/dtheta at x0 on the solved instance (host-synchronous call)
     dp.solve(stream)
@@ -449,7 +459,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": config_dict(p, world, "flushed between steps (256 MB write)"),
-        "effective_evals_per_s": world * stats["effective_evals"] * args.steps / (total_ms / 1e3),
+        "effective_evals_per_s": job_rate(stats["effective_evals"] * args.steps, world, total_ms / 1e3),
         "ms_per_solve_median": statistics.median(times),
         "ms_per_solve_p99": float(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))]),
         "rollout": {"fuel_g": traj["fuel_g"], "time_s": traj["time_s"], "J": traj["J"]},
