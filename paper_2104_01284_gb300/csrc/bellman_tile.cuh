@@ -62,12 +62,16 @@ __device__ __forceinline__ float ldv(const float *p)
     return __ldca(p);
 }
 
+// Speed blend of the two time columns as one packed multiply and one packed
+// FMA (per lane the same IEEE operations as the scalar form
+// A = wv1 p1 + (wv0 p0)), then the time blend G = wt1 B + (wt0 A).
 template <bool NC>
 __device__ __forceinline__ float blend(const float *p0, const float *p1, float wv0, float wv1, float wt0, float wt1)
 {
-    float A = __fmaf_rn(wv1, ldv<NC>(p1), __fmul_rn(wv0, ldv<NC>(p0)));
-    float B = __fmaf_rn(wv1, ldv<NC>(p1 + 1), __fmul_rn(wv0, ldv<NC>(p0 + 1)));
-    return __fmaf_rn(wt1, B, __fmul_rn(wt0, A));
+    const float2 lo = make_float2(ldv<NC>(p0), ldv<NC>(p0 + 1));
+    const float2 hi = make_float2(ldv<NC>(p1), ldv<NC>(p1 + 1));
+    const float2 AB = __ffma2_rn(make_float2(wv1, wv1), hi, __fmul2_rn(make_float2(wv0, wv0), lo));
+    return __fmaf_rn(wt1, AB.y, __fmul_rn(wt0, AB.x));
 }
 
 // Per-lane interpolation context of one class.

@@ -34,10 +34,6 @@ constexpr float V_BIG = 1e30f;
 constexpr float V_FEAS_MAX = 1e12f;
 constexpr float SNAP = 1e-5f;
 
-// Bellman kernel tiling: each thread owns RJ consecutive SoC rows at one time
-// node; controls are grouped into torque classes (see ClassRec).
-constexpr int RJ = 8;
-
 struct DevParams {
     // sizes
     int N, n_v, n_xi, n_t, n_te, n_tm, n_b, n_u;
@@ -229,18 +225,6 @@ __device__ __forceinline__ float terminal_cost(const DevParams &P, float v, floa
     float sh = fmaxf(__fsub_rn(P.soc_ref, xi), 0.f);
     float dv = __fsub_rn(v, P.v_ref);
     return __fadd_rn(__fmul_rn(P.w_soc, sh), __fmul_rn(P.w_v, __fmul_rn(dv, dv)));
-}
-
-// Bilinear blend of two speed rows (p0, p1 point at the lower time column,
-// the upper one follows it): the speed/time part of the trilinear
-// interpolation of J_{k+1}.  Every caller uses this one function so that
-// values are reproduced bit for bit.
-__device__ __forceinline__ float g_blend2(const float *__restrict__ p0, const float *__restrict__ p1, float wv0,
-                                          float wv1, float wt0, float wt1)
-{
-    float A = __fmaf_rn(wv1, __ldg(p1), __fmul_rn(wv0, __ldg(p0)));
-    float B = __fmaf_rn(wv1, __ldg(p1 + 1), __fmul_rn(wv0, __ldg(p0 + 1)));
-    return __fmaf_rn(wt1, B, __fmul_rn(wt0, A));
 }
 
 // ---- launchers (host) -------------------------------------------------------
