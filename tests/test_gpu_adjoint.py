@@ -44,26 +44,38 @@ def oracle_fd(p, support, piall):
     return np.array(fd), stable
 
 
-@pytest.mark.parametrize("seed", [100, 101, 102, 104, 105])
-def test_gpu_adjoint_matches_fp64_finite_differences(gpu, seed):
-    p = small(seed)
-    op = O.make(p)
-    Vs, _, _ = O.solve(op)
-    g_or, d, sup, rc = O.adjoint(op, X0)
-    if rc != 0:
-        pytest.skip("start state infeasible")
-    fd, stable = oracle_fd(p, sup, op._piall)
-    if not stable or d["snapped"] or d["infeasible_corner"] or d["min_gap"] < 1e-4:
-        pytest.skip("argmin not stable on the support")
-    dp = gpu(p)
-    dp.solve()
-    J, g = dp.adjoint(X0)
-    assert J == pytest.approx(O.interp(op, 0, Vs[0], *X0), rel=1e-4)
-    scale = np.maximum(np.abs(fd), 1e-6 * np.max(np.abs(fd)))
-    rel = np.abs(g - fd) / scale
-    assert np.all(rel <= 1e-3), (g, fd, rel)
-    # and the oracle's adjoint on its own solution
-    assert np.all(np.abs(g - g_or) <= 1e-3 * scale), (g, g_or)
+def test_gpu_adjoint_matches_fp64_finite_differences_on_20_stable_seeds(gpu):
+    """Seeds from 100 upward (the adjoint configuration's scan) until 20
+    problems with a stable argmin on the lam-support pass: the start state is
+    feasible, the oracle's policy on the support is the same at theta +- h for
+    every parameter, no snapped fraction or infeasible corner is on the
+    support and the best-vs-second gap exceeds 1e-4.  On each, the GPU
+    adjoint agrees with the FP64 central differences (step 1e-4 |theta|) and
+    with the oracle's own adjoint to 1e-3 relative (acceptance (e))."""
+    passed = []
+    for seed in range(100, 200):
+        p = small(seed)
+        op = O.make(p)
+        Vs, _, _ = O.solve(op)
+        g_or, d, sup, rc = O.adjoint(op, X0)
+        if rc != 0:
+            continue  # start state infeasible
+        fd, stable = oracle_fd(p, sup, op._piall)
+        if not stable or d["snapped"] or d["infeasible_corner"] or d["min_gap"] < 1e-4:
+            continue  # argmin not stable on the support
+        dp = gpu(p)
+        dp.solve()
+        J, g = dp.adjoint(X0)
+        dp.close()
+        assert J == pytest.approx(O.interp(op, 0, Vs[0], *X0), rel=1e-4), seed
+        scale = np.maximum(np.abs(fd), 1e-6 * np.max(np.abs(fd)))
+        rel = np.abs(g - fd) / scale
+        assert np.all(rel <= 1e-3), (seed, g, fd, rel)
+        assert np.all(np.abs(g - g_or) <= 1e-3 * scale), (seed, g, g_or)
+        passed.append(seed)
+        if len(passed) == 20:
+            break
+    assert len(passed) == 20, passed
 
 
 def test_autograd_function(gpu):
