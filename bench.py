@@ -421,7 +421,15 @@ def run_ours(args):
                 "envelope_evals_per_launch": stats["envelope_evals"] / p.n_stages,
                 "class_evals_per_launch": stats["class_evals"] / p.n_stages,
                 "envelope_fraction": stats["envelope_evals"] / max(1, stats["effective_evals"]),
-                "argmin_states": stats["argmin_states"]}
+                "argmin_states": stats["argmin_states"],
+                # context: the direct trilinear form evaluates every state x
+                # control with 8 FMA (16 FLOP); at this kernel's time it would
+                # need this rate, which the class factorisation and the
+                # envelopes avoid
+                "direct_form_equivalent": {
+                    "flop_per_eval": 16,
+                    "tflops": 16.0 * p.evals_per_solve / p.n_stages / per_launch_s / 1e12,
+                    "of_peak": 16.0 * p.evals_per_solve / p.n_stages / per_launch_s / 1e12 / peak}}
 
     # end to end through the public API with host buffers: upload the
     # problem tables, solve, read the trajectory back, every step
