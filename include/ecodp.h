@@ -153,8 +153,9 @@ dp_status dp_problem_destroy(dp_problem_t p);
  * are broken in the order (torque class, control index): the first class of
  * ascending total torque (brake flag fastest) that reaches the minimum, then
  * the lowest control index inside that class.  Asynchronous on stream;
- * results stay on the device.  The 2N+1 launches are captured in a CUDA graph
- * on the first call on a stream and replayed afterwards. */
+ * results stay on the device.  The sweep's launches (terminal values, the
+ * per-stage tables of all stages, then the N Bellman stages) are captured in a
+ * CUDA graph on the first call and replayed afterwards. */
 dp_status dp_solve_backward(dp_problem_t p, void *stream);
 
 /* Copy J_stage (stage in [0, N]) or pi_stage (stage in [0, N-1]) into
@@ -242,10 +243,12 @@ const char *dp_last_error(void);
 dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5]);
 
 /* Select the Bellman kernel of later solves: 1 = tiled (default: torque
- * classes, register windows, shared-memory tables), 0 = direct (one thread
- * per state, every control read separately; the layout of the paper's
- * second kernel, Sec. IV).  Both return bit-identical values and policies;
- * the direct one exists for cross-checking.  DP_ERR_INVALID_ARG otherwise. */
+ * classes, register windows, shared-memory tables; on grids whose tiles cannot
+ * fill the GPU each tile's classes are split over several CTAs and joined), 0 =
+ * direct (one thread per state, every kept control read separately; the
+ * layout of the paper's second kernel, Sec. IV).  Both return bit-identical
+ * values and policies; the direct one exists for cross-checking.
+ * DP_ERR_INVALID_ARG otherwise. */
 dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant);
 
 /* Profiling hook: run one backward sweep (same work and results as
