@@ -150,9 +150,9 @@ dp_status dp_problem_destroy(dp_problem_t p);
  * J_{k+1}; their values are lines c + f D in the difference D of those rows,
  * and only the lines on the lower envelope of each such group are evaluated
  * (the minimum is that of all controls up to FP32 rounding).  Exact FP32 ties
- * are broken in the order (torque class, control index): the first class of
- * ascending total torque (brake flag fastest) that reaches the minimum, then
- * the lowest control index inside that class.  Asynchronous on stream;
+ * are broken in the order (torque class, control index): the first class,
+ * ordered by brake flag and then by ascending total torque, that reaches the
+ * minimum, then the lowest control index inside that class.  Asynchronous on stream;
  * results stay on the device.  The sweep's launches (terminal values, the
  * per-stage tables of all stages, then the N Bellman stages) are captured in a
  * CUDA graph on the first call and replayed afterwards. */

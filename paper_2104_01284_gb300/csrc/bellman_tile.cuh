@@ -33,8 +33,8 @@
 // infeasible without a per-row select.
 //
 // Argmin order: (value, torque class, control index).  Among controls with
-// exactly equal FP32 values the first class in class order (total torque
-// ascending, brake flag fastest) wins, then the lowest control index inside
+// exactly equal FP32 values the first class in class order (brake flag
+// slowest, then total torque ascending) wins, then the lowest control index inside
 // it.  Exact FP32 ties are rounding coincidences of near-equal costs (the
 // FP64 recursion has none on the seeded instances); resolving them toward the
 // lowest global control index would re-evaluate every tied class.

@@ -78,7 +78,10 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_tiled(const DevParams *__re
     if (threadIdx.x == 0)
         P = *dP;
     __syncthreads();
-    const int i = blockIdx.y;
+    // speed rows in descending order: the CTA scheduler places CTAs round
+    // robin over the SMs, so the light low-speed rows (few feasible classes)
+    // come last and fill the SMs that received a fourth CTA
+    const int i = gridDim.y - 1 - blockIdx.y;
     const size_t row = (size_t)k * P.n_v + i;
     bellman_tile<R_SINGLE, true>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls, sc.spl + row * P.n_u,
                                  sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn, Vk, pik, i, blockIdx.x, smem_raw,

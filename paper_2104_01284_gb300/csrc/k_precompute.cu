@@ -64,6 +64,11 @@ __global__ void dense_from_pad_kernel(const DevParams P, const float *__restrict
     }
 }
 
+// Class numbering: c = b n_sum + s, where s indexes the total torque (the sum
+// i_e + i_m, or the pair (i_e, i_m) when classes are single controls) and b
+// the brake flag.  Classes of one brake flag are thus consecutive in
+// ascending torque, so consecutive classes land on neighbouring successor
+// speeds and mostly read the same cells of J_{k+1} (L1 reuse in the tile).
 // Members (i_e, i_m) of class c in increasing i_e order (increasing u).
 struct Members {
     int ie_lo, ie_hi, s;  // class_sum: i_m = s - i_e; otherwise one member
@@ -73,7 +78,7 @@ struct Members {
 __device__ __forceinline__ Members class_members(const DevParams &P, int c)
 {
     Members m;
-    int s = c / P.n_b;
+    int s = c % (P.n_cls / P.n_b);
     if (P.class_sum) {
         m.ie_lo = max(0, s - (P.n_tm - 1));
         m.ie_hi = min(s, P.n_te - 1);
@@ -91,7 +96,7 @@ __device__ __forceinline__ int member_im(const Members &m, int ie) { return m.im
 
 __device__ __forceinline__ int class_of(const DevParams &P, int ie, int im, int b)
 {
-    return (P.class_sum ? (ie + im) : (ie * P.n_tm + im)) * P.n_b + b;
+    return b * (P.n_cls / P.n_b) + (P.class_sum ? (ie + im) : (ie * P.n_tm + im));
 }
 
 // Block-wide exclusive scan of one int per thread; returns the prefix and
@@ -199,7 +204,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
 
     // 1. classes: speed update, step time, speed-axis band and interpolation
     for (int c = threadIdx.x; c < P.n_cls; c += blockDim.x) {
-        const int b = c % P.n_b;
+        const int b = c / (P.n_cls / P.n_b);
         const Members mem = class_members(P, c);
         const int ie0 = mem.ie_lo, im0 = member_im(mem, ie0);
         const float T =
@@ -268,7 +273,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     // {-2, -1, 0, 1}) pair, one pair per thread (members are disjoint)
     for (int task = threadIdx.x; task < P.n_cls * 4; task += blockDim.x) {
         const int c = task >> 2, bucket = task & 3;
-        bucket_envelope(P, class_members(P, c), c % P.n_b, bucket - 2, s_ctrl);
+        bucket_envelope(P, class_members(P, c), c / (P.n_cls / P.n_b), bucket - 2, s_ctrl);
     }
     __syncthreads();
 
@@ -282,7 +287,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         int nspl = 0, nfeas = 0;
         if (c < P.n_cls) {
             mem = class_members(P, c);
-            const int b = c % P.n_b;
+            const int b = c / (P.n_cls / P.n_b);
             for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
                 const CtrlRec r = s_ctrl[(ie * P.n_tm + member_im(mem, ie)) * P.n_b + b];
                 if (r.ok) {
@@ -299,7 +304,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         const int spl_off = block_exclusive_scan(nspl, scan_buf, spl_tot) + spl_carry;
         block_exclusive_scan(nfeas, scan_buf, feas_tot);
         if (feas) {
-            const int b = c % P.n_b;
+            const int b = c / (P.n_cls / P.n_b);
             ClassEntry E;
             E.cls = c;
             E.off = spl_off;
