@@ -65,13 +65,18 @@ __device__ __forceinline__ float ldv(const float *p)
 // Speed blend of the two time columns as one packed multiply and one packed
 // FMA (per lane the same IEEE operations as the scalar form
 // A = wv1 p1 + (wv0 p0)), then the time blend G = wt1 B + (wt0 A).
+__device__ __forceinline__ float blend_raw(float2 lo, float2 hi, float wv0, float wv1, float wt0, float wt1)
+{
+    const float2 AB = __ffma2_rn(make_float2(wv1, wv1), hi, __fmul2_rn(make_float2(wv0, wv0), lo));
+    return __fmaf_rn(wt1, AB.y, __fmul_rn(wt0, AB.x));
+}
+
 template <bool NC>
 __device__ __forceinline__ float blend(const float *p0, const float *p1, float wv0, float wv1, float wt0, float wt1)
 {
     const float2 lo = make_float2(ldv<NC>(p0), ldv<NC>(p0 + 1));
     const float2 hi = make_float2(ldv<NC>(p1), ldv<NC>(p1 + 1));
-    const float2 AB = __ffma2_rn(make_float2(wv1, wv1), hi, __fmul2_rn(make_float2(wv0, wv0), lo));
-    return __fmaf_rn(wt1, AB.y, __fmul_rn(wt0, AB.x));
+    return blend_raw(lo, hi, wv0, wv1, wt0, wt1);
 }
 
 // Per-lane interpolation context of one class.
@@ -294,6 +299,43 @@ __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x,
     return ub;
 }
 
+// Window of one class: blended values at SoC rows jb - 2 .. jb + R + 1 (row
+// offsets roff); the outermost two only where a bucket d = -2 (lo_end) or
+// d = +1 (hi_end) needs them.
+template <int R, bool NC>
+__device__ __forceinline__ void class_window(const TCtx &x, const int (&roff)[R + 4], bool lo_end, bool hi_end,
+                                             float (&G)[R + 4])
+{
+#pragma unroll
+    for (int w = 1; w < R + 3; ++w)
+        G[w] = blend<NC>(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
+    G[0] = G[R + 3] = 0.f;
+    if (lo_end)
+        G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
+    if (hi_end)
+        G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
+}
+
+// Windows of two classes that read the same corners (same pointers in x)
+// with their own weights: G with x's, H with (bv0, bv1, bt0, bt1); each
+// corner is loaded once.
+template <int R, bool NC>
+__device__ __forceinline__ void pair_window(const TCtx &x, const int (&roff)[R + 4], float bv0, float bv1, float bt0,
+                                            float bt1, bool lo_end, bool hi_end, float (&G)[R + 4], float (&H)[R + 4])
+{
+#pragma unroll
+    for (int w = 0; w < R + 4; ++w) {
+        G[w] = H[w] = 0.f;
+        if ((w == 0 && !lo_end) || (w == R + 3 && !hi_end))
+            continue;
+        const float *p0 = x.p0 + roff[w], *p1 = x.p1 + roff[w];
+        const float2 lo = make_float2(ldv<NC>(p0), ldv<NC>(p0 + 1));
+        const float2 hi = make_float2(ldv<NC>(p1), ldv<NC>(p1 + 1));
+        G[w] = blend_raw(lo, hi, x.wv0, x.wv1, x.wt0, x.wt1);
+        H[w] = blend_raw(lo, hi, bv0, bv1, bt0, bt1);
+    }
+}
+
 // Shared memory of a tile: the row's tables (classes, class entries, lines as
 // {c, f} and their control indices; a line outside the four buckets reads its
 // shift from the global table), then per warp the argmin-recovery buffers:
@@ -417,21 +459,41 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     }
     const int e_lo = MODE == TILE_SLICE ? e_begin : 0;
     const int e_hi = MODE == TILE_SLICE ? min(e_end, n_ent) : (MODE == TILE_JOIN ? 0 : n_ent);
+    // Consecutive classes with the same speed cell and time shift read the
+    // same four corners of J_{k+1} and differ only in their weights.  Where
+    // the corners depend neither on the class nor on the lane (no red check
+    // at the next node, no waiting row), such a pair loads its window once:
+    // H keeps the second class's values for the next iteration.
+    const bool can_pair = !si.wait_row && !(P.light_model != 1 && si.next_light >= 0);
+    float H[R + 4];
+    bool have_h = false;
     for (int e = e_lo; e < e_hi; ++e) {
         const ClassEntry E = s_ent[e];
-        const TCtx x = class_ctx(P, Vn, s_cls[E.cls], l, tl, wait, si);
+        const ClassRec C = s_cls[E.cls];
+        const TCtx x = class_ctx(P, Vn, C, l, tl, wait, si);
         // window rows jb - 2 .. jb + R + 1; the outermost two only for the
         // buckets d = -2 and d = +1 (warp-uniform: E is the same in every lane)
         float G[R + 4];
         float Dg[R + 3];
+        if (have_h) {
 #pragma unroll
-        for (int w = 1; w < R + 3; ++w)
-            G[w] = blend<NC>(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
-        G[0] = G[R + 3] = 0.f;
-        if (E.nb[0] > 0)
-            G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
-        if (E.nb[3] > 0)
-            G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
+            for (int w = 0; w < R + 4; ++w)
+                G[w] = H[w];
+            have_h = false;
+        } else {
+            ClassEntry E2;
+            ClassRec C2;
+            if (can_pair && e + 1 < e_hi) {
+                E2 = s_ent[e + 1];
+                C2 = s_cls[E2.cls];
+                have_h = C2.iv == C.iv && C2.st == C.st;
+            }
+            if (have_h)
+                pair_window<R, NC>(x, roff, __fsub_rn(1.f, C2.fv), C2.fv, __fsub_rn(1.f, C2.ft), C2.ft,
+                                   E.nb[0] > 0 || E2.nb[0] > 0, E.nb[3] > 0 || E2.nb[3] > 0, G, H);
+            else
+                class_window<R, NC>(x, roff, E.nb[0] > 0, E.nb[3] > 0, G);
+        }
 #pragma unroll
         for (int w = 0; w < R + 3; ++w)
             Dg[w] = __fsub_rn(G[w + 1], G[w]);
