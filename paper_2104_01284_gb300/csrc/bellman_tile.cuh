@@ -273,7 +273,7 @@ __device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float
 // if none), re-evaluated with exactly the arithmetic of the sweep.
 template <bool NC>
 __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x, const ClassEntry &E,
-                                              const float2 *ln, const unsigned short *us, const SplitRec *g_spl,
+                                              const float2 *ln, const SplitRec *g_spl,
                                               int j, float bv)
 {
     float g5[5];  // SoC rows j - 2 .. j + 2
@@ -284,17 +284,16 @@ __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x,
     int q = E.off;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {  // bucket b holds the shift d = b - 2
-        for (int n = 0; n < E.nb[b]; ++n, ++q) {
-            const int u = us[q];
-            if (split_value(ln[q].x, ln[q].y, g5[b], g5[b + 1]) == bv && u < ub)
-                ub = u;
-        }
+        for (int n = 0; n < E.nb[b]; ++n, ++q)
+            if (split_value(ln[q].x, ln[q].y, g5[b], g5[b + 1]) == bv)
+                ub = min(ub, split_u(g_spl[q]));
     }
     for (int n = 0; n < E.n_other; ++n, ++q) {
         const float2 a = ln[q];
-        const int d = split_d(g_spl[q]), u = us[q];
-        if (split_value(a.x, a.y, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv && u < ub)
-            ub = u;
+        const SplitRec S = g_spl[q];
+        const int d = split_d(S);
+        if (split_value(a.x, a.y, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv)
+            ub = min(ub, split_u(S));
     }
     return ub;
 }
@@ -336,12 +335,68 @@ __device__ __forceinline__ void pair_window(const TCtx &x, const int (&roff)[R +
     }
 }
 
-// Shared memory of a tile: the row's tables (classes, class entries, lines as
-// {c, f} and their control indices; a line outside the four buckets reads its
-// shift from the global table), then per warp the argmin-recovery buffers:
-// counters [n_cls + 1], entry list [32 R], best value per state [32 R].
+// A feasible class as a tile stages it, in entry order (32 bytes, half of
+// its ClassRec + ClassEntry): speed cell iv, time shift st (clamped to 2^14,
+// beyond any time grid) and the flag v' > 0 packed in one word, the weights,
+// the step time, and where its lines start and how many each bucket holds.
+struct TileClass {
+    unsigned ivst;  // iv | min(st, 2^14) << 16 | (v' > 0) << 31
+    float fv, ft, dt;
+    int off;
+    unsigned nb4;   // lines of the buckets d = -2, -1, 0, +1, one byte each
+    int n_other;
+    int pad;
+};
+
+__device__ __forceinline__ TileClass tile_class(const ClassRec &C, const ClassEntry &E)
+{
+    TileClass T;
+    T.ivst = (unsigned)C.iv | ((unsigned)min(C.st, 1 << 14) << 16) | (C.v1 > 0.f ? 0x80000000u : 0u);
+    T.fv = C.fv;
+    T.ft = C.ft;
+    T.dt = C.dt;
+    T.off = E.off;
+    T.nb4 = (unsigned)E.nb[0] | ((unsigned)E.nb[1] << 8) | ((unsigned)E.nb[2] << 16) | ((unsigned)E.nb[3] << 24);
+    T.n_other = E.n_other;
+    T.pad = 0;
+    return T;
+}
+
+// The fields of ClassRec that the tile reads (v1 only through v1 > 0).
+__device__ __forceinline__ ClassRec tile_rec(const TileClass &T)
+{
+    ClassRec C = {};
+    C.ok = 1;
+    C.iv = (int)(T.ivst & 0xffffu);
+    C.st = (int)((T.ivst >> 16) & 0x7fffu);
+    C.v1 = (T.ivst >> 31) ? 1.f : 0.f;
+    C.fv = T.fv;
+    C.ft = T.ft;
+    C.dt = T.dt;
+    return C;
+}
+
+__device__ __forceinline__ ClassEntry tile_entry(const TileClass &T, int e)
+{
+    ClassEntry E;
+    E.cls = e;
+    E.off = T.off;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        E.nb[b] = (int)((T.nb4 >> (8 * b)) & 0xffu);
+    E.n_other = T.n_other;
+    E.n_total = 0;
+    return E;
+}
+
+// Shared memory of a tile: the row's feasible classes (TileClass) and lines
+// as {c, f} (a line outside the four buckets reads its shift, and argmin
+// recovery its control index, from the global table), then per warp the
+// argmin-recovery buffers: counters [n_cls + 1], entry list [32 R], best
+// value per state [32 R].  Kept small: the rest of the SM's 256 KB of L1 and
+// shared memory caches the J_{k+1} windows.
 struct Layout {
-    size_t ent, line, bits, warp, warp_bytes, total;
+    size_t line, warp, warp_bytes, total;
     size_t w_list, w_best;  // offsets inside a warp's block
 };
 
@@ -349,13 +404,9 @@ template <int R>
 __host__ __device__ inline Layout layout(int n_cls, int n_u)
 {
     Layout L;
-    size_t o = (size_t)n_cls * sizeof(ClassRec);
-    L.ent = o;
-    o += (size_t)n_cls * sizeof(ClassEntry);
+    size_t o = (size_t)n_cls * sizeof(TileClass);
     L.line = o;
     o += ((size_t)n_u * sizeof(float2) + 15) / 16 * 16;
-    L.bits = o;
-    o += ((size_t)n_u * sizeof(unsigned short) + 15) / 16 * 16;
     L.warp = o;
     size_t w = ((size_t)(n_cls + 1) * sizeof(int) + 15) / 16 * 16;
     L.w_list = w;
@@ -401,24 +452,17 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
 {
     const int tid = threadIdx.x;
     const Layout L = layout<R>(P.n_cls, P.n_u);
-    ClassRec *s_cls = reinterpret_cast<ClassRec *>(smem_raw);
-    ClassEntry *s_ent = reinterpret_cast<ClassEntry *>(smem_raw + L.ent);
+    TileClass *s_tc = reinterpret_cast<TileClass *>(smem_raw);
     float2 *s_line = reinterpret_cast<float2 *>(smem_raw + L.line);
-    unsigned short *s_u = reinterpret_cast<unsigned short *>(smem_raw + L.bits);
     __syncthreads();  // the previous tile may still read the tables
     {
-        const int4 *src = reinterpret_cast<const int4 *>(g_cls);
-        int4 *dst = reinterpret_cast<int4 *>(s_cls);
-        for (int q = tid; q < P.n_cls * 2; q += TLANES)
-            dst[q] = src[q];
-        const int4 *src2 = reinterpret_cast<const int4 *>(g_ent);
-        int4 *dst2 = reinterpret_cast<int4 *>(s_ent);
-        for (int q = tid; q < n_ent * 2; q += TLANES)
-            dst2[q] = src2[q];
+        for (int q = tid; q < n_ent; q += TLANES) {
+            const ClassEntry E = g_ent[q];
+            s_tc[q] = tile_class(g_cls[E.cls], E);
+        }
         for (int q = tid; q < n_spl; q += TLANES) {
             const SplitRec S = g_spl[q];
             s_line[q] = make_float2(S.c, S.f);
-            s_u[q] = (unsigned short)split_u(S);
         }
     }
     const int warp = tid >> 5, lane = tid & 31;
@@ -468,8 +512,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     float H[R + 4];
     bool have_h = false;
     for (int e = e_lo; e < e_hi; ++e) {
-        const ClassEntry E = s_ent[e];
-        const ClassRec C = s_cls[E.cls];
+        const TileClass T = s_tc[e];
+        const ClassEntry E = tile_entry(T, e);
+        const ClassRec C = tile_rec(T);
         const TCtx x = class_ctx(P, Vn, C, l, tl, wait, si);
         // window rows jb - 2 .. jb + R + 1; the outermost two only for the
         // buckets d = -2 and d = +1 (warp-uniform: E is the same in every lane)
@@ -484,8 +529,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             ClassEntry E2;
             ClassRec C2;
             if (can_pair && e + 1 < e_hi) {
-                E2 = s_ent[e + 1];
-                C2 = s_cls[E2.cls];
+                const TileClass T2 = s_tc[e + 1];
+                E2 = tile_entry(T2, e + 1);
+                C2 = tile_rec(T2);
                 have_h = C2.iv == C.iv && C2.st == C.st;
             }
             if (have_h)
@@ -638,11 +684,12 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const int lq = fq - jgq * P.n_t;
         const float tlq = node_val(P.t_lo, P.t_span, lq, P.n_t);
         const float wq = wait_time(tb, k, tlq, si.wait_row);
-        const ClassEntry E = s_ent[e];
-        const TCtx x = class_ctx(P, Vn, s_cls[E.cls], lq, tlq, wq, si);
+        const TileClass T = s_tc[e];
+        const ClassEntry E = tile_entry(T, e);
+        const TCtx x = class_ctx(P, Vn, tile_rec(T), lq, tlq, wq, si);
         const int j = jgq * R + r;
         pik[((size_t)i * P.n_xi + j) * P.n_t + lq] =
-            (int16_t)class_lowest_u<NC>(P, x, E, s_line, s_u, g_spl, j, w_best[s]);
+            (int16_t)class_lowest_u<NC>(P, x, E, s_line, g_spl, j, w_best[s]);
     }
 }
 
