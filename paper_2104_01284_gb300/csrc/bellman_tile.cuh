@@ -456,11 +456,22 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     float2 *s_line = reinterpret_cast<float2 *>(smem_raw + L.line);
     __syncthreads();  // the previous tile may still read the tables
     {
-        for (int q = tid; q < n_ent; q += TLANES) {
+        // a slice stages only its own classes and their lines (same indices)
+        int c_lo = 0, c_hi = n_ent, q_lo = 0, q_hi = n_spl;
+        if (MODE == TILE_SLICE) {
+            c_lo = e_begin;
+            c_hi = min(e_end, n_ent);
+            q_lo = q_hi = 0;
+            if (c_lo < c_hi) {
+                q_lo = g_ent[c_lo].off;
+                q_hi = g_ent[c_hi - 1].off + g_ent[c_hi - 1].n_total;
+            }
+        }
+        for (int q = c_lo + tid; q < c_hi; q += TLANES) {
             const ClassEntry E = g_ent[q];
             s_tc[q] = tile_class(g_cls[E.cls], E);
         }
-        for (int q = tid; q < n_spl; q += TLANES) {
+        for (int q = q_lo + tid; q < q_hi; q += TLANES) {
             const SplitRec S = g_spl[q];
             s_line[q] = make_float2(S.c, S.f);
         }
