@@ -92,43 +92,67 @@ struct StageInfo {
     float cyc1, red1, off1;
 };
 
-__device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, const ClassRec &C, int l, float tl,
-                                          float wait, const StageInfo &si)
+// The step time dt and whether v' > 0, read only on a waiting row and before
+// a light (through a callback, so a tile reads them from shared memory only
+// there).
+struct DtFlag {
+    float dt;
+    bool moving;  // v' > 0
+};
+
+template <class DtFn>
+__device__ __forceinline__ TCtx class_ctx_at(const DevParams &P, const float *Vn, int iv, int st, float fv, float ft_c,
+                                             DtFn dtv, int l, float tl, float wait, const StageInfo &si)
 {
     TCtx x;
     int t0;
     float ft;
     if (!si.wait_row) {
-        t0 = l + C.st;
-        ft = C.ft;
-    } else {
-        int st;
-        snap_split(__fdiv_rn(__fadd_rn(wait, C.dt), P.h_t), st, ft);
         t0 = l + st;
+        ft = ft_c;
+    } else {
+        int sw;
+        snap_split(__fdiv_rn(__fadd_rn(wait, dtv().dt), P.h_t), sw, ft);
+        t0 = l + sw;
     }
     // an arrival during red at the next node (Eq. 5c, 7c, 8) makes every
     // value of the class infeasible: read the padding columns, which hold
     // V_BIG in every row
     bool red = false;
-    if (P.light_model != 1 && si.next_light >= 0 && C.v1 > 0.f) {
-        const float tarr = __fadd_rn(__fadd_rn(tl, wait), C.dt);
-        red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
+    if (P.light_model != 1 && si.next_light >= 0) {
+        const DtFlag d = dtv();
+        if (d.moving) {
+            const float tarr = __fadd_rn(__fadd_rn(tl, wait), d.dt);
+            red = phase_pos(tarr, si.off1, si.cyc1) < si.red1;
+        }
     }
     // literal Eq. 5c: departing from the line needs green (no folded wait);
     // the zero-speed step (v' = 0) lands at the end of red
-    if (P.light_model == 2 && si.wait_row && wait > 0.f && C.v1 > 0.f)
+    if (P.light_model == 2 && si.wait_row && wait > 0.f && dtv().moving)
         red = true;
     // a lower corner past the grid reads the padding column n_t; the upper
     // corner is the next column, still inside the row (ld_t >= n_t + 2)
     const int ta = red ? P.n_t : min(t0, P.n_t);
     x.wt1 = ft;
     x.wt0 = __fsub_rn(1.f, ft);
-    x.wv1 = C.fv;
-    x.wv0 = __fsub_rn(1.f, C.fv);
+    x.wv1 = fv;
+    x.wv0 = __fsub_rn(1.f, fv);
     const size_t vrow = (size_t)P.xi_rows * P.ld_t;
-    x.p0 = Vn + (size_t)C.iv * vrow + ta;
+    x.p0 = Vn + (size_t)iv * vrow + ta;
     x.p1 = x.p0 + vrow;
     return x;
+}
+
+// dt's bits with bit 31 set when v' = 0 (dt is never negative)
+__device__ __forceinline__ unsigned dt_flagged(const ClassRec &C)
+{
+    return __float_as_uint(C.dt) | (C.v1 > 0.f ? 0u : 0x80000000u);
+}
+
+__device__ __forceinline__ TCtx class_ctx(const DevParams &P, const float *Vn, const ClassRec &C, int l, float tl,
+                                          float wait, const StageInfo &si)
+{
+    return class_ctx_at(P, Vn, C.iv, C.st, C.fv, C.ft, [&] { return DtFlag{C.dt, C.v1 > 0.f}; }, l, tl, wait, si);
 }
 
 __device__ __forceinline__ int row_offset(const DevParams &P, int j)
@@ -245,10 +269,9 @@ __device__ __forceinline__ void bucket_min(const float2 *ln, int n, const float2
     }
 }
 
-// One bucket's candidates G[r + D + 2] + cm[r] folded into the class minimum
-// (the first bucket of the class initialises it).
+// One bucket's candidates G[r + D + 2] + cm[r] folded into the class minimum.
 template <int R, int D>
-__device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float (&cm)[R], float (&cls)[R], bool first)
+__device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float (&cm)[R], float (&cls)[R])
 {
     float cand[R];
     if ((D & 1) == 0) {
@@ -266,7 +289,7 @@ __device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        cls[r] = first ? cand[r] : fminf(cls[r], cand[r]);
+        cls[r] = fminf(cls[r], cand[r]);
 }
 
 // Lowest control index of class E whose value at SoC row j equals bv (INT_MAX
@@ -335,45 +358,32 @@ __device__ __forceinline__ void pair_window(const TCtx &x, const int (&roff)[R +
     }
 }
 
-// A feasible class as a tile stages it, in entry order (32 bytes, half of
-// its ClassRec + ClassEntry): speed cell iv, time shift st (clamped to 2^14,
-// beyond any time grid) and the flag v' > 0 packed in one word, the weights,
-// the step time, and where its lines start and how many each bucket holds.
+// A feasible class as a tile stages it, in entry order (32 bytes): speed
+// cell iv and time shift st in one word (st clamped to 2^14, beyond any time
+// grid; a pair compares the word), the weights, the first line, and the line
+// counts of the buckets d = -2 .. +1 (the last word also holds the count of
+// lines with any other shift in its upper half).  The step time, read only on
+// waiting rows and before a light, sits in a separate array.
 struct TileClass {
-    unsigned ivst;  // iv | min(st, 2^14) << 16 | (v' > 0) << 31
-    float fv, ft, dt;
+    unsigned ivst;  // iv | min(st, 2^14) << 16
+    float fv, ft;
     int off;
-    unsigned nb4;   // lines of the buckets d = -2, -1, 0, +1, one byte each
-    int n_other;
-    int pad;
+    int nb0, nb1, nb2;
+    unsigned nb3_other;  // nb3 | n_other << 16
 };
 
 __device__ __forceinline__ TileClass tile_class(const ClassRec &C, const ClassEntry &E)
 {
     TileClass T;
-    T.ivst = (unsigned)C.iv | ((unsigned)min(C.st, 1 << 14) << 16) | (C.v1 > 0.f ? 0x80000000u : 0u);
+    T.ivst = (unsigned)C.iv | ((unsigned)min(C.st, 1 << 14) << 16);
     T.fv = C.fv;
     T.ft = C.ft;
-    T.dt = C.dt;
     T.off = E.off;
-    T.nb4 = (unsigned)E.nb[0] | ((unsigned)E.nb[1] << 8) | ((unsigned)E.nb[2] << 16) | ((unsigned)E.nb[3] << 24);
-    T.n_other = E.n_other;
-    T.pad = 0;
+    T.nb0 = E.nb[0];
+    T.nb1 = E.nb[1];
+    T.nb2 = E.nb[2];
+    T.nb3_other = (unsigned)E.nb[3] | ((unsigned)E.n_other << 16);
     return T;
-}
-
-// The fields of ClassRec that the tile reads (v1 only through v1 > 0).
-__device__ __forceinline__ ClassRec tile_rec(const TileClass &T)
-{
-    ClassRec C = {};
-    C.ok = 1;
-    C.iv = (int)(T.ivst & 0xffffu);
-    C.st = (int)((T.ivst >> 16) & 0x7fffu);
-    C.v1 = (T.ivst >> 31) ? 1.f : 0.f;
-    C.fv = T.fv;
-    C.ft = T.ft;
-    C.dt = T.dt;
-    return C;
 }
 
 __device__ __forceinline__ ClassEntry tile_entry(const TileClass &T, int e)
@@ -381,22 +391,36 @@ __device__ __forceinline__ ClassEntry tile_entry(const TileClass &T, int e)
     ClassEntry E;
     E.cls = e;
     E.off = T.off;
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        E.nb[b] = (int)((T.nb4 >> (8 * b)) & 0xffu);
-    E.n_other = T.n_other;
+    E.nb[0] = T.nb0;
+    E.nb[1] = T.nb1;
+    E.nb[2] = T.nb2;
+    E.nb[3] = (int)(T.nb3_other & 0xffffu);
+    E.n_other = (int)(T.nb3_other >> 16);
     E.n_total = 0;
     return E;
 }
 
-// Shared memory of a tile: the row's feasible classes (TileClass) and lines
-// as {c, f} (a line outside the four buckets reads its shift, and argmin
-// recovery its control index, from the global table), then per warp the
-// argmin-recovery buffers: counters [n_cls + 1], entry list [32 R], best
-// value per state [32 R].  Kept small: the rest of the SM's 256 KB of L1 and
-// shared memory caches the J_{k+1} windows.
+__device__ __forceinline__ TCtx tile_ctx(const DevParams &P, const float *Vn, const TileClass &T,
+                                         const unsigned *s_dtv, int e, int l, float tl, float wait,
+                                         const StageInfo &si)
+{
+    return class_ctx_at(
+        P, Vn, (int)(T.ivst & 0xffffu), (int)(T.ivst >> 16), T.fv, T.ft,
+        [&] {
+            const unsigned b = s_dtv[e];
+            return DtFlag{__uint_as_float(b & 0x7fffffffu), (b >> 31) == 0u};
+        },
+        l, tl, wait, si);
+}
+
+// Shared memory of a tile: the row's feasible classes (TileClass, then the
+// flagged step times) and lines as {c, f} (a line outside the four buckets
+// reads its shift, and argmin recovery its control index, from the global
+// table), then per warp the argmin-recovery buffers: counters [n_cls + 1],
+// entry list [32 R], best value per state [32 R].  Kept small: the rest of
+// the SM's 256 KB of L1 and shared memory caches the J_{k+1} windows.
 struct Layout {
-    size_t line, warp, warp_bytes, total;
+    size_t dtv, line, warp, warp_bytes, total;
     size_t w_list, w_best;  // offsets inside a warp's block
 };
 
@@ -405,6 +429,8 @@ __host__ __device__ inline Layout layout(int n_cls, int n_u)
 {
     Layout L;
     size_t o = (size_t)n_cls * sizeof(TileClass);
+    L.dtv = o;
+    o += ((size_t)n_cls * sizeof(float) + 15) / 16 * 16;
     L.line = o;
     o += ((size_t)n_u * sizeof(float2) + 15) / 16 * 16;
     L.warp = o;
@@ -453,6 +479,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     const int tid = threadIdx.x;
     const Layout L = layout<R>(P.n_cls, P.n_u);
     TileClass *s_tc = reinterpret_cast<TileClass *>(smem_raw);
+    unsigned *s_dtv = reinterpret_cast<unsigned *>(smem_raw + L.dtv);
     float2 *s_line = reinterpret_cast<float2 *>(smem_raw + L.line);
     __syncthreads();  // the previous tile may still read the tables
     {
@@ -469,7 +496,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         }
         for (int q = c_lo + tid; q < c_hi; q += TLANES) {
             const ClassEntry E = g_ent[q];
-            s_tc[q] = tile_class(g_cls[E.cls], E);
+            const ClassRec C = g_cls[E.cls];
+            s_tc[q] = tile_class(C, E);
+            s_dtv[q] = dt_flagged(C);
         }
         for (int q = q_lo + tid; q < q_hi; q += TLANES) {
             const SplitRec S = g_spl[q];
@@ -525,8 +554,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     for (int e = e_lo; e < e_hi; ++e) {
         const TileClass T = s_tc[e];
         const ClassEntry E = tile_entry(T, e);
-        const ClassRec C = tile_rec(T);
-        const TCtx x = class_ctx(P, Vn, C, l, tl, wait, si);
+        const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
         // window rows jb - 2 .. jb + R + 1; the outermost two only for the
         // buckets d = -2 and d = +1 (warp-uniform: E is the same in every lane)
         float G[R + 4];
@@ -537,17 +565,14 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 G[w] = H[w];
             have_h = false;
         } else {
-            ClassEntry E2;
-            ClassRec C2;
+            TileClass T2;
             if (can_pair && e + 1 < e_hi) {
-                const TileClass T2 = s_tc[e + 1];
-                E2 = tile_entry(T2, e + 1);
-                C2 = tile_rec(T2);
-                have_h = C2.iv == C.iv && C2.st == C.st;
+                T2 = s_tc[e + 1];
+                have_h = T2.ivst == T.ivst;
             }
             if (have_h)
-                pair_window<R, NC>(x, roff, __fsub_rn(1.f, C2.fv), C2.fv, __fsub_rn(1.f, C2.ft), C2.ft,
-                                   E.nb[0] > 0 || E2.nb[0] > 0, E.nb[3] > 0 || E2.nb[3] > 0, G, H);
+                pair_window<R, NC>(x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft,
+                                   E.nb[0] > 0 || T2.nb0 > 0, E.nb[3] > 0 || (T2.nb3_other & 0xffffu) > 0, G, H);
             else
                 class_window<R, NC>(x, roff, E.nb[0] > 0, E.nb[3] > 0, G);
         }
@@ -562,13 +587,14 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         }
         float cls_min[R];
         float cm[R];
-        bool first = true;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            cls_min[r] = __int_as_float(0x7f800000);
         int q = E.off;
 #define ECODP_BUCKET(B, D)                                      \
         if (E.nb[B] > 0) {                                      \
             bucket_min<R, D>(s_line + q, E.nb[B], EV, OD, cm);  \
-            bucket_fold<R, D>(G, cm, cls_min, first);           \
-            first = false;                                      \
+            bucket_fold<R, D>(G, cm, cls_min);                  \
             q += E.nb[B];                                       \
         }
         ECODP_BUCKET(0, -2)
@@ -576,11 +602,6 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         ECODP_BUCKET(2, 0)
         ECODP_BUCKET(3, 1)
 #undef ECODP_BUCKET
-        if (first) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                cls_min[r] = __int_as_float(0x7f800000);
-        }
         for (int n = 0; n < E.n_other; ++n, ++q) {
             const float2 a = s_line[q];
             const int d = split_d(g_spl[q]);
@@ -697,7 +718,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const float wq = wait_time(tb, k, tlq, si.wait_row);
         const TileClass T = s_tc[e];
         const ClassEntry E = tile_entry(T, e);
-        const TCtx x = class_ctx(P, Vn, tile_rec(T), lq, tlq, wq, si);
+        const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, lq, tlq, wq, si);
         const int j = jgq * R + r;
         pik[((size_t)i * P.n_xi + j) * P.n_t + lq] =
             (int16_t)class_lowest_u<NC>(P, x, E, s_line, g_spl, j, w_best[s]);
