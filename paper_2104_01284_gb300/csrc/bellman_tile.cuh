@@ -321,6 +321,34 @@ __device__ __forceinline__ int class_lowest_u(const DevParams &P, const TCtx &x,
     return ub;
 }
 
+// class_lowest_u on the row's global table (the per-state join).
+template <bool NC>
+__device__ __forceinline__ int class_lowest_u_global(const DevParams &P, const TCtx &x, const ClassEntry &E,
+                                                     const SplitRec *g_spl, int j, float bv)
+{
+    float g5[5];  // SoC rows j - 2 .. j + 2
+#pragma unroll
+    for (int w = 0; w < 5; ++w)
+        g5[w] = g_at<NC>(P, x, j - 2 + w);
+    int ub = INT_MAX;
+    int q = E.off;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {  // bucket b holds the shift d = b - 2
+        for (int n = 0; n < E.nb[b]; ++n, ++q) {
+            const SplitRec S = g_spl[q];
+            if (split_value(S.c, S.f, g5[b], g5[b + 1]) == bv)
+                ub = min(ub, split_u(S));
+        }
+    }
+    for (int n = 0; n < E.n_other; ++n, ++q) {
+        const SplitRec S = g_spl[q];
+        const int d = split_d(S);
+        if (split_value(S.c, S.f, g_at<NC>(P, x, j + d), g_at<NC>(P, x, j + d + 1)) == bv)
+            ub = min(ub, split_u(S));
+    }
+    return ub;
+}
+
 // Window of one class: blended values at SoC rows jb - 2 .. jb + R + 1 (row
 // offsets roff); the outermost two only where a bucket d = -2 (lo_end) or
 // d = +1 (hi_end) needs them.
@@ -455,13 +483,13 @@ __host__ __device__ inline int chunks_per_row(int n_xi, int n_t)
 // are (cls, ent, spl) with n_ent feasible classes and n_spl controls.  All
 // TLANES threads of the CTA call it; it starts with a barrier so the shared
 // memory can be reused by the next tile.
-// Tile modes: the whole class list (TILE_FULL); a slice [e_begin, e_end) of
-// it whose per-state minimum, packed as (value bits << 32 | class), is
+// Tile modes: the whole class list (TILE_FULL), or a slice [e_begin, e_end)
+// of it whose per-state minimum, packed as (value bits << 32 | class), is
 // merged into `part` with atomicMin (TILE_SLICE: values are non-negative, so
 // their bit patterns order like the floats, and equal values keep the lower
-// class, the tie order below); or the join of the slices (TILE_JOIN: read and
-// reset `part`, then write J_k and recover the argmin exactly as TILE_FULL).
-constexpr int TILE_FULL = 0, TILE_SLICE = 1, TILE_JOIN = 2;
+// class, the tie order below); a per-state join then writes J_k and recovers
+// the argmin from `part`.
+constexpr int TILE_FULL = 0, TILE_SLICE = 1;
 
 __device__ __forceinline__ unsigned long long pack_min(float v, int e)
 {
@@ -542,7 +570,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         bcls[r] = 0;
     }
     const int e_lo = MODE == TILE_SLICE ? e_begin : 0;
-    const int e_hi = MODE == TILE_SLICE ? min(e_end, n_ent) : (MODE == TILE_JOIN ? 0 : n_ent);
+    const int e_hi = MODE == TILE_SLICE ? min(e_end, n_ent) : n_ent;
     // Consecutive classes with the same speed cell and time shift read the
     // same four corners of J_{k+1} and differ only in their weights.  Where
     // the corners depend neither on the class nor on the lane (no red check
@@ -629,22 +657,6 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         }
         return;
     }
-    if (MODE == TILE_JOIN) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int j = jb + r;
-            if (f_ok && j < P.n_xi) {
-                unsigned long long *q = part + ((size_t)i * P.n_xi + j) * P.n_t + l;
-                const unsigned long long w = *q;
-                *q = ~0ull;  // ready for the next stage
-                if (w != ~0ull) {
-                    best[r] = __uint_as_float((unsigned)(w >> 32));
-                    bcls[r] = (int)(unsigned)(w & 0xffffffffu);
-                }
-            }
-        }
-    }
-
     // values now; argmin recovery below
     const bool masked = sampled_red(P, tb, si, v, tl);
     unsigned todo = 0;

@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_tiled(const DevParams *__re
 }
 
 // Class-split tiles for grids whose tiles cannot fill the GPU: blockIdx.z
-// picks one of gridDim.z slices of the row's class list; a join launch then
-// writes J_k and the argmin (TILE_SLICE / TILE_JOIN in bellman_tile.cuh).
+// picks one of gridDim.z slices of the row's class list (TILE_SLICE in
+// bellman_tile.cuh); a per-state join launch then writes J_k and the argmin.
 __global__ void __launch_bounds__(TLANES, 4) bellman_slice(const DevParams *__restrict__ dP, StageTables tb, int k,
                                                           StageScratch sc, const float *__restrict__ Vn)
 {
@@ -111,20 +111,47 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_slice(const DevParams *__re
                                              nullptr, i, blockIdx.x, smem_raw, nullptr, e0, e1, sc.part);
 }
 
-__global__ void __launch_bounds__(TLANES, 4) bellman_join(const DevParams *__restrict__ dP, StageTables tb, int k,
-                                                         StageScratch sc, const float *__restrict__ Vn,
-                                                         float *__restrict__ Vk, int16_t *__restrict__ pik)
+// Join of the class-split slices, one thread per state: the packed minimum
+// in `part` (value bits << 32 | class entry) gives J_k, and the lowest control
+// of the winning class that reaches the value is recovered with the sweep's
+// arithmetic; `part` is reset for the next stage.
+__global__ void __launch_bounds__(256) bellman_join(const DevParams *__restrict__ dP, StageTables tb, int k,
+                                                    StageScratch sc, const float *__restrict__ Vn,
+                                                    float *__restrict__ Vk, int16_t *__restrict__ pik)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevParams P;
     if (threadIdx.x == 0)
         P = *dP;
     __syncthreads();
     const int i = blockIdx.y;
-    const size_t row = (size_t)k * P.n_v + i;
-    bellman_tile<R_SINGLE, true, TILE_JOIN>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
-                                            sc.spl + row * P.n_u, sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn,
-                                            Vk, pik, i, blockIdx.x, smem_raw, sc.stats, 0, 0, sc.part);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    bool found = false;
+    if (s < P.n_xi * P.n_t) {
+        const int j = s / P.n_t, l = s % P.n_t;
+        const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
+        const float tl = node_val(P.t_lo, P.t_span, l, P.n_t);
+        const StageInfo si = stage_info(tb, k, v);
+        const float wait = wait_time(tb, k, tl, si.wait_row);
+        const size_t row = (size_t)k * P.n_v + i;
+        const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + l;
+        const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
+        const unsigned long long w = sc.part[op];
+        sc.part[op] = ~0ull;
+        const float best = w != ~0ull ? __uint_as_float((unsigned)(w >> 32)) : __int_as_float(0x7f800000);
+        if (best < V_FEAS_MAX && !sampled_red(P, tb, si, v, tl)) {
+            const ClassEntry E = sc.ent[row * P.n_cls + (int)(unsigned)(w & 0xffffffffu)];
+            const TCtx x = class_ctx(P, Vn, sc.cls[row * P.n_cls + E.cls], l, tl, wait, si);
+            Vk[o] = __fadd_rn(best, __fmul_rn(__fsub_rn(1.f, P.gamma), wait));
+            pik[op] = (int16_t)class_lowest_u_global<true>(P, x, E, sc.spl + row * P.n_u, j, best);
+            found = true;
+        } else {
+            Vk[o] = V_BIG;
+            pik[op] = -1;
+        }
+    }
+    const unsigned n_find = __reduce_add_sync(0xffffffffu, found ? 1u : 0u);
+    if (sc.stats && (threadIdx.x & 31) == 0 && n_find)
+        atomicAdd(sc.stats + 3, (unsigned long long)n_find);
 }
 
 // Class slices per tile: as many as keep the GPU's resident CTA slots (4 per
@@ -162,14 +189,11 @@ cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables
             cudaFuncSetAttribute(bellman_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return err;
-        err = cudaFuncSetAttribute(bellman_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess)
-            return err;
         bellman_slice<<<dim3(chunks, hP.n_v, slices), TLANES, smem, s>>>(dP, tb, k, sc, Vnext);
         err = cudaGetLastError();
         if (err != cudaSuccess)
             return err;
-        bellman_join<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
+        bellman_join<<<dim3((hP.n_xi * hP.n_t + 255) / 256, hP.n_v), 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
         return cudaGetLastError();
     }
     cudaError_t err = cudaFuncSetAttribute(bellman_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
