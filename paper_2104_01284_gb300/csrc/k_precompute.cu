@@ -270,10 +270,22 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     __syncthreads();
 
     // 3. the lower envelope of every (class, SoC-shift bucket d in
-    // {-2, -1, 0, 1}) pair, one pair per thread (members are disjoint)
-    for (int task = threadIdx.x; task < P.n_cls * 4; task += blockDim.x) {
-        const int c = task >> 2, bucket = task & 3;
-        bucket_envelope(P, class_members(P, c), c / (P.n_cls / P.n_b), bucket - 2, s_ctrl);
+    // {-2, -1, 0, 1}) pair, one pair per task (members are disjoint).  An
+    // envelope costs ~m^2 for m members: tasks are ranked by decreasing class
+    // size (the total torques nearest the middle of their range first) and
+    // dealt out in a snake, so a thread's heavy task of one round pairs with
+    // a light one of the next.
+    const int n_sum = P.n_cls / P.n_b;
+    for (int k = 0;; ++k) {
+        const int task = k * blockDim.x + ((k & 1) ? blockDim.x - 1 - threadIdx.x : threadIdx.x);
+        if (k * blockDim.x >= P.n_cls * 4)
+            break;
+        if (task >= P.n_cls * 4)
+            continue;
+        const int rank = task >> 2, bucket = task & 3;
+        const int b = rank % P.n_b, q = rank / P.n_b, mid = (n_sum - 1) / 2;
+        const int c = b * n_sum + mid + ((q & 1) ? (q + 1) / 2 : -(q / 2));
+        bucket_envelope(P, class_members(P, c), b, bucket - 2, s_ctrl);
     }
     __syncthreads();
 
