@@ -349,35 +349,25 @@ __device__ __forceinline__ int class_lowest_u_global(const DevParams &P, const T
     return ub;
 }
 
-// Window of one class: blended values at SoC rows jb - 2 .. jb + R + 1 (row
-// offsets roff); the outermost two only where a bucket d = -2 (lo_end) or
-// d = +1 (hi_end) needs them.
+// Inner window of one class: blended values at SoC rows jb - 1 .. jb + R
+// (G[1 .. R + 2]; row offsets roff), which the buckets d = -1 and d = 0 read.
 template <int R, bool NC>
-__device__ __forceinline__ void class_window(const TCtx &x, const int (&roff)[R + 4], bool lo_end, bool hi_end,
-                                             float (&G)[R + 4])
+__device__ __forceinline__ void class_window(const TCtx &x, const int (&roff)[R + 4], float (&G)[R + 4])
 {
 #pragma unroll
     for (int w = 1; w < R + 3; ++w)
         G[w] = blend<NC>(x.p0 + roff[w], x.p1 + roff[w], x.wv0, x.wv1, x.wt0, x.wt1);
-    G[0] = G[R + 3] = 0.f;
-    if (lo_end)
-        G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
-    if (hi_end)
-        G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
 }
 
-// Windows of two classes that read the same corners (same pointers in x)
-// with their own weights: G with x's, H with (bv0, bv1, bt0, bt1); each
+// Inner windows of two classes that read the same corners (same pointers in
+// x) with their own weights: G with x's, H with (bv0, bv1, bt0, bt1); each
 // corner is loaded once.
 template <int R, bool NC>
 __device__ __forceinline__ void pair_window(const TCtx &x, const int (&roff)[R + 4], float bv0, float bv1, float bt0,
-                                            float bt1, bool lo_end, bool hi_end, float (&G)[R + 4], float (&H)[R + 4])
+                                            float bt1, float (&G)[R + 4], float (&H)[R + 4])
 {
 #pragma unroll
-    for (int w = 0; w < R + 4; ++w) {
-        G[w] = H[w] = 0.f;
-        if ((w == 0 && !lo_end) || (w == R + 3 && !hi_end))
-            continue;
+    for (int w = 1; w < R + 3; ++w) {
         const float *p0 = x.p0 + roff[w], *p1 = x.p1 + roff[w];
         const float2 lo = make_float2(ldv<NC>(p0), ldv<NC>(p0 + 1));
         const float2 hi = make_float2(ldv<NC>(p1), ldv<NC>(p1 + 1));
@@ -583,13 +573,12 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const TileClass T = s_tc[e];
         const ClassEntry E = tile_entry(T, e);
         const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
-        // window rows jb - 2 .. jb + R + 1; the outermost two only for the
-        // buckets d = -2 and d = +1 (warp-uniform: E is the same in every lane)
+        // inner window rows jb - 1 .. jb + R (G[1 .. R + 2]); the outer rows
+        // G[0], G[R + 3] only for the rare buckets d = -2, +1 below
         float G[R + 4];
-        float Dg[R + 3];
         if (have_h) {
 #pragma unroll
-            for (int w = 0; w < R + 4; ++w)
+            for (int w = 1; w < R + 3; ++w)
                 G[w] = H[w];
             have_h = false;
         } else {
@@ -599,18 +588,21 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 have_h = T2.ivst == T.ivst;
             }
             if (have_h)
-                pair_window<R, NC>(x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft,
-                                   E.nb[0] > 0 || T2.nb0 > 0, E.nb[3] > 0 || (T2.nb3_other & 0xffffu) > 0, G, H);
+                pair_window<R, NC>(x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft, G, H);
             else
-                class_window<R, NC>(x, roff, E.nb[0] > 0, E.nb[3] > 0, G);
+                class_window<R, NC>(x, roff, G);
         }
+        // SoC differences Dg[w] = G[w + 1] - G[w] as even-aligned pairs EV[p]
+        // = {Dg[2p], Dg[2p + 1]} and odd-aligned pairs OD[p] = {Dg[2p + 1],
+        // Dg[2p + 2]}; the inner buckets read EV[1 .. R/2] and OD[0 .. R/2 - 1]
+        float Dg[R + 3];
 #pragma unroll
-        for (int w = 0; w < R + 3; ++w)
+        for (int w = 1; w < R + 2; ++w)
             Dg[w] = __fsub_rn(G[w + 1], G[w]);
         float2 EV[R / 2 + 1], OD[R / 2 + 1];
 #pragma unroll
-        for (int p = 0; p < R / 2 + 1; ++p) {
-            EV[p] = make_float2(Dg[2 * p], Dg[2 * p + 1]);
+        for (int p = 0; p < R / 2; ++p) {
+            EV[p + 1] = make_float2(Dg[2 * p + 2], Dg[2 * p + 3]);
             OD[p] = make_float2(Dg[2 * p + 1], Dg[2 * p + 2]);
         }
         float cls_min[R];
@@ -618,26 +610,43 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
 #pragma unroll
         for (int r = 0; r < R; ++r)
             cls_min[r] = __int_as_float(0x7f800000);
-        int q = E.off;
-#define ECODP_BUCKET(B, D)                                      \
-        if (E.nb[B] > 0) {                                      \
-            bucket_min<R, D>(s_line + q, E.nb[B], EV, OD, cm);  \
-            bucket_fold<R, D>(G, cm, cls_min);                  \
-            q += E.nb[B];                                       \
+        const int q1 = E.off + E.nb[0], q2 = q1 + E.nb[1];
+        if (E.nb[1] > 0) {
+            bucket_min<R, -1>(s_line + q1, E.nb[1], EV, OD, cm);
+            bucket_fold<R, -1>(G, cm, cls_min);
         }
-        ECODP_BUCKET(0, -2)
-        ECODP_BUCKET(1, -1)
-        ECODP_BUCKET(2, 0)
-        ECODP_BUCKET(3, 1)
-#undef ECODP_BUCKET
-        for (int n = 0; n < E.n_other; ++n, ++q) {
-            const float2 a = s_line[q];
-            const int d = split_d(g_spl[q]);
-            const float c = a.x, f = a.y;
+        if (E.nb[2] > 0) {
+            bucket_min<R, 0>(s_line + q2, E.nb[2], EV, OD, cm);
+            bucket_fold<R, 0>(G, cm, cls_min);
+        }
+        // rare (warp-uniform): the outer buckets d = -2, +1 and the lines of
+        // any other shift
+        if ((E.nb[0] | E.nb[3] | E.n_other) != 0) {
+            G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
+            G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
+            Dg[0] = __fsub_rn(G[1], G[0]);
+            Dg[R + 2] = __fsub_rn(G[R + 3], G[R + 2]);
+            EV[0] = make_float2(Dg[0], Dg[1]);
+            OD[R / 2] = make_float2(Dg[R + 1], Dg[R + 2]);
+            if (E.nb[0] > 0) {
+                bucket_min<R, -2>(s_line + E.off, E.nb[0], EV, OD, cm);
+                bucket_fold<R, -2>(G, cm, cls_min);
+            }
+            const int q3 = q2 + E.nb[2];
+            if (E.nb[3] > 0) {
+                bucket_min<R, 1>(s_line + q3, E.nb[3], EV, OD, cm);
+                bucket_fold<R, 1>(G, cm, cls_min);
+            }
+            int q = q3 + E.nb[3];
+            for (int n = 0; n < E.n_other; ++n, ++q) {
+                const float2 a = s_line[q];
+                const int d = split_d(g_spl[q]);
+                const float c = a.x, f = a.y;
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                cls_min[r] = fminf(cls_min[r],
-                                   split_value(c, f, g_at<NC>(P, x, jb + r + d), g_at<NC>(P, x, jb + r + d + 1)));
+                for (int r = 0; r < R; ++r)
+                    cls_min[r] = fminf(cls_min[r], split_value(c, f, g_at<NC>(P, x, jb + r + d),
+                                                               g_at<NC>(P, x, jb + r + d + 1)));
+            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {

@@ -168,3 +168,21 @@ def test_dependency_wait_timeout_is_reported(mods):
             dp.solve()
             assert torch.equal(bt.value(b, 0), dp.value(0))
             dp.close()
+
+
+def test_batch_with_wide_soc_shifts_equals_alone(mods):
+    """Instances whose SoC cell shifts span -5 .. +3 (small battery: outer
+    buckets and lines of other shifts) beside ordinary ones: every instance
+    of the persistent launch equals its single solve bit for bit."""
+    from tests.test_gpu_parity import reduced
+    probs = [reduced(seed=56).replace(capacity_As=450.0), reduced(seed=57),
+             reduced(seed=58, n_soc=27).replace(capacity_As=300.0)]
+    for R in (8, 4):
+        with mods.EcoDPBatch(probs, rows_per_lane=R) as bt:
+            bt.solve()
+            for b, p in enumerate(probs):
+                V, pi, _ = solve_alone(mods, p)
+                for k in range(p.n_stages + 1):
+                    assert np.array_equal(bits(bt.value(b, k).cpu().numpy()), bits(V[k])), (R, b, k)
+                for k in range(p.n_stages):
+                    assert np.array_equal(bt.policy(b, k).cpu().numpy(), pi[k]), (R, b, k)

@@ -64,6 +64,9 @@ PROBLEMS = {
     "reduced_s2": lambda: reduced(seed=32, n_soc=11, n_t=33, n_te=7, n_tm=9),  # unequal torque steps
     # the grid of the paper's Table I: 690 controls, one torque class each
     "paper_grid": lambda: P.paper_table1(),
+    # a small battery: SoC cell shifts -5 .. +3 per step, so the outer buckets
+    # d = -2, +1 and lines of other shifts are taken (elsewhere d is -1 or 0)
+    "wide_shift": lambda: reduced(seed=56).replace(capacity_As=450.0),
 }
 
 
@@ -112,7 +115,7 @@ def feasible_start(p, V0, V0lo, V0hi):
     return (float(vg[i]), float(sg[j]), float(tg[l]))
 
 
-@pytest.mark.parametrize("name", ["c0", "reduced", "paper_grid"])
+@pytest.mark.parametrize("name", ["c0", "reduced", "paper_grid", "wide_shift"])
 def test_end_to_end_parity_and_rollout(gpu, name):
     p = PROBLEMS[name]()
     op = O.make(p)
