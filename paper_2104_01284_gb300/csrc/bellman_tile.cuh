@@ -224,9 +224,9 @@ __device__ __forceinline__ float wait_time(const StageTables &tb, int k, float t
 }
 
 // Minimum over the lines of one SoC-shift bucket: row r takes
-// min_u (c_u + f_u D[r + D + 2]).  Lines are staged as {c, c, f, f} so each
-// gives its two packed operands directly.  EV holds the even-aligned
-// difference pairs {D[2p], D[2p+1]}, OD the odd-aligned pairs {D[2p+1], D[2p+2]}.
+// min_u (c_u + f_u D[r + D + 2]).  Lines are staged as {c, f}; a packed FMA
+// evaluates one line at two SoC rows.  EV holds the even-aligned difference
+// pairs {D[2p], D[2p+1]}, OD the odd-aligned pairs {D[2p+1], D[2p+2]}.
 template <int R, int D>
 __device__ __forceinline__ void bucket_min(const float2 *ln, int n, const float2 (&EV)[R / 2 + 1],
                                            const float2 (&OD)[R / 2 + 1], float (&cm)[R])
@@ -269,8 +269,9 @@ __device__ __forceinline__ void bucket_min(const float2 *ln, int n, const float2
     }
 }
 
-// One bucket's candidates G[r + D + 2] + cm[r] folded into the class minimum.
-template <int R, int D>
+// One bucket's candidates G[r + D + 2] + cm[r] folded into the class minimum
+// (FIRST: they start it).
+template <int R, int D, bool FIRST = false>
 __device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float (&cm)[R], float (&cls)[R])
 {
     float cand[R];
@@ -289,7 +290,7 @@ __device__ __forceinline__ void bucket_fold(const float (&G)[R + 4], const float
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        cls[r] = fminf(cls[r], cand[r]);
+        cls[r] = FIRST ? cand[r] : fminf(cls[r], cand[r]);
 }
 
 // Lowest control index of class E whose value at SoC row j equals bv (INT_MAX
@@ -607,13 +608,14 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         }
         float cls_min[R];
         float cm[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            cls_min[r] = __int_as_float(0x7f800000);
         const int q1 = E.off + E.nb[0], q2 = q1 + E.nb[1];
         if (E.nb[1] > 0) {
             bucket_min<R, -1>(s_line + q1, E.nb[1], EV, OD, cm);
-            bucket_fold<R, -1>(G, cm, cls_min);
+            bucket_fold<R, -1, true>(G, cm, cls_min);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                cls_min[r] = __int_as_float(0x7f800000);
         }
         if (E.nb[2] > 0) {
             bucket_min<R, 0>(s_line + q2, E.nb[2], EV, OD, cm);
