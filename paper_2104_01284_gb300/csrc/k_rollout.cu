@@ -1,12 +1,16 @@
 // Forward rollout (trajectory extraction, the simulation step of Sec. V).
 //
-// One CTA walks the N stages from x0.  At every stage each thread evaluates
-// a strided subset of the controls at the continuous state: the one-step
-// model (Eq. 2, 5a-5c), the constraints (Eq. 7, 8) and the trilinear
-// interpolation of J_{k+1} at the continuous successor; a block argmin
-// (lowest control index on ties) selects the control, which is applied.
-// Cumulative time, fuel and cost are summed in FP64.
+// A cluster of CTAs (one CTA per instance in the batched form) walks the N
+// stages from x0.  At every stage each thread evaluates a strided subset of
+// the controls at the continuous state: the one-step model (Eq. 2, 5a-5c), the
+// constraints (Eq. 7, 8) and the trilinear interpolation of J_{k+1} at the
+// continuous successor; an argmin over the CTA, then over the cluster through
+// distributed shared memory (lowest control index on ties), selects the
+// control, which every CTA applies to its copy of the state.  Cumulative time,
+// fuel and cost are summed in FP64.
 #include <climits>
+
+#include <cooperative_groups.h>
 
 #include "ecodp_internal.cuh"
 
@@ -122,11 +126,20 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
 }
 
 constexpr int ROLL_THREADS = 1024;
+constexpr int ROLL_CLUSTER = 8;  // CTAs (SMs) of the single-problem rollout
 
-// The rollout of one problem by the whole CTA over stages [k_begin, k_end).
-// A later segment continues from the state, fuel, cost and fail stage the
-// previous one left in `out`; the terminal cost is added by the segment
-// that ends at stage N.
+// A CTA's best control of a stage.
+struct Cand {
+    float F;
+    int u;
+    Step s;
+};
+
+// The rollout of one problem by a cluster of CS CTAs over stages
+// [k_begin, k_end).  A later segment continues from the state, fuel, cost and
+// fail stage the previous one left in `out`; the terminal cost is added by
+// the segment that ends at stage N.  CTA rank 0 writes the outputs.
+template <int CS>
 __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables &tb, const StageView &view,
                              int k_begin, int k_end, double v0, double xi0, double t0, double *__restrict__ out,
                              int *__restrict__ out_u)
@@ -136,8 +149,14 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     __shared__ double s_t, s_fuel, s_J;
     __shared__ float red_F[ROLL_THREADS / 32];
     __shared__ int red_u[ROLL_THREADS / 32];
-    __shared__ int s_fail, s_win;
-    __shared__ Step s_step;
+    __shared__ int s_fail;
+    // this CTA's candidate, double-buffered by stage parity: the cluster's
+    // CTAs read it after the stage's cluster barrier, and a CTA can only
+    // rewrite a buffer after the next barrier, when every CTA has read it
+    __shared__ Cand s_cand[2];
+    unsigned rank = 0;
+    if constexpr (CS > 1)
+        rank = cooperative_groups::this_cluster().block_rank();
     if (threadIdx.x == 0)
         P = *dP;
     __syncthreads();
@@ -170,79 +189,122 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     __syncthreads();
     if (s_fail >= 0)
         return;  // an earlier segment found no feasible control
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = k_begin; k < k_end; ++k) {
         const float v = s_v, xi = s_xi, t = (float)s_t;
         const float *Vn = view.at(k + 1);
         float bF = __int_as_float(0x7f800000);
         int bu = INT_MAX;
         Step bs = {};
-        for (int u = threadIdx.x; u < P.n_u; u += blockDim.x) {
-            Step s;
-            if (!model_step(P, tb, k, v, xi, t, u, s))
-                continue;
-            float F = __fadd_rn(s.cost, interp_cont(P, Vn, s.v1, s.xi1, __fadd_rn(__fadd_rn(t, s.wait), s.dt)));
-            if (F < V_FEAS_MAX && (F < bF || (F == bF && u < bu))) {
-                bF = F;
-                bu = u;
-                bs = s;
+        // CTA r of the cluster takes the controls u = r (mod CS), two per
+        // thread and pass, so their loads of J_{k+1} overlap
+        for (int i0 = threadIdx.x;; i0 += 2 * (int)blockDim.x) {
+            const int u0 = i0 * CS + (int)rank, u1 = (i0 + (int)blockDim.x) * CS + (int)rank;
+            if (u0 >= P.n_u)
+                break;
+            Step s0, s1;
+            const bool ok0 = model_step(P, tb, k, v, xi, t, u0, s0);
+            const bool ok1 = u1 < P.n_u && model_step(P, tb, k, v, xi, t, u1, s1);
+            const float F0 =
+                ok0 ? __fadd_rn(s0.cost, interp_cont(P, Vn, s0.v1, s0.xi1, __fadd_rn(__fadd_rn(t, s0.wait), s0.dt)))
+                    : V_BIG;
+            const float F1 =
+                ok1 ? __fadd_rn(s1.cost, interp_cont(P, Vn, s1.v1, s1.xi1, __fadd_rn(__fadd_rn(t, s1.wait), s1.dt)))
+                    : V_BIG;
+            if (ok0 && F0 < V_FEAS_MAX && (F0 < bF || (F0 == bF && u0 < bu))) {
+                bF = F0;
+                bu = u0;
+                bs = s0;
+            }
+            if (ok1 && F1 < V_FEAS_MAX && (F1 < bF || (F1 == bF && u1 < bu))) {
+                bF = F1;
+                bu = u1;
+                bs = s1;
             }
         }
         const int my_u = bu;
-        // block argmin on (F, u)
+        // block argmin on (F, u): within each warp, then every warp reduces
+        // the warps' results itself, so all threads know the winner
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            float oF = __shfl_down_sync(0xffffffffu, bF, off);
-            int ou = __shfl_down_sync(0xffffffffu, bu, off);
+            const float oF = __shfl_down_sync(0xffffffffu, bF, off);
+            const int ou = __shfl_down_sync(0xffffffffu, bu, off);
             if (oF < bF || (oF == bF && ou < bu)) {
                 bF = oF;
                 bu = ou;
             }
         }
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) {
             red_F[warp] = bF;
             red_u[warp] = bu;
         }
         __syncthreads();
+        const int n_warps = (int)(blockDim.x >> 5);
+        bF = lane < n_warps ? red_F[lane] : __int_as_float(0x7f800000);
+        bu = lane < n_warps ? red_u[lane] : INT_MAX;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oF = __shfl_xor_sync(0xffffffffu, bF, off);
+            const int ou = __shfl_xor_sync(0xffffffffu, bu, off);
+            if (oF < bF || (oF == bF && ou < bu)) {
+                bF = oF;
+                bu = ou;
+            }
+        }
+        // the CTA's winner publishes its candidate (thread 0 an empty one)
+        Cand *mine = &s_cand[k & 1];
+        if (bu == INT_MAX) {
+            if (threadIdx.x == 0) {
+                mine->F = __int_as_float(0x7f800000);
+                mine->u = INT_MAX;
+            }
+        } else if (my_u == bu) {
+            mine->F = bF;
+            mine->u = bu;
+            mine->s = bs;
+        }
+        if constexpr (CS > 1)
+            cooperative_groups::this_cluster().sync();
+        else
+            __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-                if (red_F[w] < bF || (red_F[w] == bF && red_u[w] < bu)) {
-                    bF = red_F[w];
-                    bu = red_u[w];
+            // the cluster's winner, lowest control index on ties
+            Cand w = *mine;
+            if constexpr (CS > 1) {
+                cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+#pragma unroll
+                for (int r = 0; r < CS; ++r) {
+                    const Cand c = *cl.map_shared_rank(mine, (unsigned)r);
+                    if (c.F < w.F || (c.F == w.F && c.u < w.u))
+                        w = c;
                 }
             }
-            s_win = bu;
-        }
-        __syncthreads();
-        if (my_u == s_win && my_u != INT_MAX)
-            s_step = bs;  // the winning thread hands over its step record
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            bu = s_win;
-            if (bu == INT_MAX) {
+            if (w.u == INT_MAX) {
                 s_fail = k;
             } else {
-                const Step s = s_step;
-                out_u[k] = bu;
-                o_dt[k] = s.dt;
-                o_wait[k] = s.wait;
+                const Step s = w.s;
                 const double fk = (double)s.mf * (double)s.dt;
-                o_fuel[k] = fk;
                 s_fuel += fk;
                 s_J += (double)s.cost;
                 s_t += (double)s.wait + (double)s.dt;
                 s_v = s.v1;
                 s_xi = s.xi1;
-                traj[3 * (k + 1) + 0] = s.v1;
-                traj[3 * (k + 1) + 1] = s.xi1;
-                traj[3 * (k + 1) + 2] = s_t;
+                if (rank == 0) {
+                    out_u[k] = w.u;
+                    o_dt[k] = s.dt;
+                    o_wait[k] = s.wait;
+                    o_fuel[k] = fk;
+                    traj[3 * (k + 1) + 0] = s.v1;
+                    traj[3 * (k + 1) + 1] = s.xi1;
+                    traj[3 * (k + 1) + 2] = s_t;
+                }
             }
         }
         __syncthreads();
         if (s_fail >= 0)
             break;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && rank == 0) {
         o_tot[0] = s_fuel;
         o_tot[1] = s_t - traj[2];
         o_tot[3] = (double)s_fail;
@@ -251,14 +313,16 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
         else
             o_tot[2] = k_end == N ? s_J + (double)terminal_cost(P, s_v, s_xi) : s_J;
     }
+    // no CTA leaves while another may still read its candidates
+    if constexpr (CS > 1)
+        cooperative_groups::this_cluster().sync();
 }
 
-__global__ void __launch_bounds__(ROLL_THREADS) rollout_kernel(const DevParams *__restrict__ dP, StageTables tb,
-                                                               StageView view, int k_begin, int k_end, double v0,
-                                                               double xi0, double t0, double *__restrict__ out,
-                                                               int *__restrict__ out_u)
+__global__ void __cluster_dims__(ROLL_CLUSTER, 1, 1) __launch_bounds__(ROLL_THREADS)
+    rollout_kernel(const DevParams *__restrict__ dP, StageTables tb, StageView view, int k_begin, int k_end,
+                   double v0, double xi0, double t0, double *__restrict__ out, int *__restrict__ out_u)
 {
-    rollout_body(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
+    rollout_body<ROLL_CLUSTER>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
 }
 
 // Batched: one CTA per instance; instance b writes its output block at
@@ -271,7 +335,7 @@ __global__ void __launch_bounds__(ROLL_THREADS)
     const int b = blockIdx.x;
     const BatchInst &I = inst[b];
     const StageView view = StageView::all(I.V, I.stage_elems);
-    rollout_body(params + b, I.tb, view, 0, I.N, x0[3 * b], x0[3 * b + 1], x0[3 * b + 2], out + out_off[b],
+    rollout_body<1>(params + b, I.tb, view, 0, I.N, x0[3 * b], x0[3 * b + 1], x0[3 * b + 2], out + out_off[b],
                  out_u + u_off[b]);
 }
 
@@ -280,7 +344,7 @@ __global__ void __launch_bounds__(ROLL_THREADS)
 cudaError_t launch_rollout(const DevParams *dP, StageTables tb, const StageView &view, int k_begin, int k_end,
                            double v0, double xi0, double t0, double *out, int *out_u, cudaStream_t s)
 {
-    rollout_kernel<<<1, ROLL_THREADS, 0, s>>>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
+    rollout_kernel<<<ROLL_CLUSTER, ROLL_THREADS, 0, s>>>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
     return cudaGetLastError();
 }
 
