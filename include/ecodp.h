@@ -244,11 +244,12 @@ dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5]);
 
 /* Select the Bellman kernel of later solves: 1 = tiled (default: torque
  * classes, register windows, shared-memory tables; on grids whose tiles cannot
- * fill the GPU each tile's classes are split over several CTAs and joined), 0 =
- * direct (one thread per state, every kept control read separately; the
- * layout of the paper's second kernel, Sec. IV).  Both return bit-identical
- * values and policies; the direct one exists for cross-checking.
- * DP_ERR_INVALID_ARG otherwise. */
+ * fill the GPU each tile's classes are split over several CTAs and joined; a
+ * lane holds 8 SoC rows, or 6 where that fills the lanes at least 15 % better),
+ * 2 / 3 = tiled with 8 / 6 SoC rows per lane forced, 0 = direct (one thread per
+ * state, every kept control read separately; the layout of the paper's second
+ * kernel, Sec. IV).  All return bit-identical values and policies; the direct
+ * one exists for cross-checking.  DP_ERR_INVALID_ARG otherwise. */
 dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant);
 
 /* Profiling hook: run one backward sweep (same work and results as

@@ -695,8 +695,8 @@ dp_status dp_set_checkpointing(dp_problem_t p, int32_t every)
 
 dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant)
 {
-    if (!p || (variant != 0 && variant != 1))
-        return fail(DP_ERR_INVALID_ARG, "variant must be 0 (direct) or 1 (tiled)");
+    if (!p || variant < 0 || variant > 3)
+        return fail(DP_ERR_INVALID_ARG, "variant must be 0 (direct), 1 (tiled), 2 (tiled, 8 rows) or 3 (tiled, 6 rows)");
     if (variant != p->variant) {
         p->variant = variant;
         if (p->gexec)

@@ -16,7 +16,11 @@ namespace {
 
 using namespace tile;
 
-constexpr int R_SINGLE = 8;  // SoC rows per lane of the single-problem kernel
+// SoC rows per lane of the single-problem kernels: 8, or 6 where it fills
+// the lanes markedly better (tile_rows); CTAs per SM the register budget is
+// sized for: 4 at 8 rows (128 registers), 5 at 6 rows (96 registers).
+template <int R>
+constexpr int tile_minb() { return R == 8 ? 4 : 5; }
 
 __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restrict__ dP, StageTables tb, int k,
                                                       StageScratch sc, const float *__restrict__ Vn,
@@ -69,9 +73,10 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     }
 }
 
-__global__ void __launch_bounds__(TLANES, 4) bellman_tiled(const DevParams *__restrict__ dP, StageTables tb, int k,
-                                                          StageScratch sc, const float *__restrict__ Vn,
-                                                          float *__restrict__ Vk, int16_t *__restrict__ pik)
+template <int R>
+__global__ void __launch_bounds__(TLANES, tile_minb<R>())
+    bellman_tiled(const DevParams *__restrict__ dP, StageTables tb, int k, StageScratch sc,
+                  const float *__restrict__ Vn, float *__restrict__ Vk, int16_t *__restrict__ pik)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevParams P;
@@ -83,16 +88,18 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_tiled(const DevParams *__re
     // come last and fill the SMs that received a fourth CTA
     const int i = gridDim.y - 1 - blockIdx.y;
     const size_t row = (size_t)k * P.n_v + i;
-    bellman_tile<R_SINGLE, true>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls, sc.spl + row * P.n_u,
-                                 sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn, Vk, pik, i, blockIdx.x, smem_raw,
-                                 sc.stats);
+    bellman_tile<R, true>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls, sc.spl + row * P.n_u,
+                          sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn, Vk, pik, i, blockIdx.x, smem_raw,
+                          sc.stats);
 }
 
 // Class-split tiles for grids whose tiles cannot fill the GPU: blockIdx.z
 // picks one of gridDim.z slices of the row's class list (TILE_SLICE in
 // bellman_tile.cuh); a per-state join launch then writes J_k and the argmin.
-__global__ void __launch_bounds__(TLANES, 4) bellman_slice(const DevParams *__restrict__ dP, StageTables tb, int k,
-                                                          StageScratch sc, const float *__restrict__ Vn)
+template <int R>
+__global__ void __launch_bounds__(TLANES, tile_minb<R>())
+    bellman_slice(const DevParams *__restrict__ dP, StageTables tb, int k, StageScratch sc,
+                  const float *__restrict__ Vn)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevParams P;
@@ -106,9 +113,9 @@ __global__ void __launch_bounds__(TLANES, 4) bellman_slice(const DevParams *__re
     const int e1 = (int)((long long)n_ent * (blockIdx.z + 1) / gridDim.z);
     if (e0 >= e1)
         return;  // an empty slice (uniform over the CTA)
-    bellman_tile<R_SINGLE, true, TILE_SLICE>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
-                                             sc.spl + row * P.n_u, n_ent, sc.row_cnt[2 * row + 1], Vn, nullptr,
-                                             nullptr, i, blockIdx.x, smem_raw, nullptr, e0, e1, sc.part);
+    bellman_tile<R, true, TILE_SLICE>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
+                                      sc.spl + row * P.n_u, n_ent, sc.row_cnt[2 * row + 1], Vn, nullptr, nullptr,
+                                      i, blockIdx.x, smem_raw, nullptr, e0, e1, sc.part);
 }
 
 // Join of the class-split slices, one thread per state: the packed minimum
@@ -169,9 +176,57 @@ int class_slices(int tiles)
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
 
+// Fraction of a launch's lanes that hold a real state with R SoC rows per
+// lane: SoC groups padded to R rows, flattened (group, time) lanes padded to
+// whole 128-lane tiles.
+double lane_fill(int R, int n_xi, int n_t)
+{
+    const int groups = (n_xi + R - 1) / R;
+    const long long flat = (long long)groups * n_t;
+    const long long lanes = (flat + TLANES - 1) / TLANES * TLANES;
+    return (double)n_xi / (groups * R) * (double)flat / (double)lanes;
+}
+
+// 6 rows per lane where they fill the lanes at least 15 % better than 8
+// (measured per-state cost of 6 rows: ~5 % above 8), else 8.
+int tile_rows(const DevParams &hP)
+{
+    return lane_fill(6, hP.n_xi, hP.n_t) > 1.15 * lane_fill(8, hP.n_xi, hP.n_t) ? 6 : 8;
+}
+
+template <int R>
+cudaError_t launch_tiles(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
+                         const float *Vnext, float *Vk, int16_t *pik, cudaStream_t s)
+{
+    const size_t smem = layout<R>(hP.n_cls, hP.n_u).total;
+    const int chunks = chunks_per_row<R>(hP.n_xi, hP.n_t);
+    const int slices = sc.part ? class_slices(chunks * hP.n_v) : 1;
+    if (slices > 1) {
+        cudaError_t err =
+            cudaFuncSetAttribute(bellman_slice<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+        bellman_slice<R><<<dim3(chunks, hP.n_v, slices), TLANES, smem, s>>>(dP, tb, k, sc, Vnext);
+        err = cudaGetLastError();
+        if (err != cudaSuccess)
+            return err;
+        bellman_join<<<dim3((hP.n_xi * hP.n_t + 255) / 256, hP.n_v), 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
+        return cudaGetLastError();
+    }
+    cudaError_t err = cudaFuncSetAttribute(bellman_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess)
+        return err;
+    bellman_tiled<R><<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t bellman_smem_bytes(const DevParams &hP) { return layout<R_SINGLE>(hP.n_cls, hP.n_u).total; }
+size_t bellman_smem_bytes(const DevParams &hP)
+{
+    const size_t a = layout<6>(hP.n_cls, hP.n_u).total, b = layout<8>(hP.n_cls, hP.n_u).total;
+    return a > b ? a : b;
+}
 
 cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
                            const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s)
@@ -181,26 +236,9 @@ cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables
         bellman_direct<<<grid, 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
         return cudaGetLastError();
     }
-    const size_t smem = bellman_smem_bytes(hP);
-    const int chunks = chunks_per_row<R_SINGLE>(hP.n_xi, hP.n_t);
-    const int slices = sc.part ? class_slices(chunks * hP.n_v) : 1;
-    if (slices > 1) {
-        cudaError_t err =
-            cudaFuncSetAttribute(bellman_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess)
-            return err;
-        bellman_slice<<<dim3(chunks, hP.n_v, slices), TLANES, smem, s>>>(dP, tb, k, sc, Vnext);
-        err = cudaGetLastError();
-        if (err != cudaSuccess)
-            return err;
-        bellman_join<<<dim3((hP.n_xi * hP.n_t + 255) / 256, hP.n_v), 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
-        return cudaGetLastError();
-    }
-    cudaError_t err = cudaFuncSetAttribute(bellman_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess)
-        return err;
-    bellman_tiled<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
-    return cudaGetLastError();
+    const int R = variant == 2 ? 8 : (variant == 3 ? 6 : tile_rows(hP));
+    return R == 6 ? launch_tiles<6>(dP, hP, tb, k, sc, Vnext, Vk, pik, s)
+                  : launch_tiles<8>(dP, hP, tb, k, sc, Vnext, Vk, pik, s);
 }
 
 }  // namespace ecodp

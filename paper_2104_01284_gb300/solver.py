@@ -141,7 +141,8 @@ class EcoDP:
         self.checkpoint_every = int(every)
 
     def set_variant(self, variant: str):
-        N.check(N.dp_set_kernel_variant(self.h, {"direct": 0, "tiled": 1}[variant]), "dp_set_kernel_variant")
+        N.check(N.dp_set_kernel_variant(self.h, {"direct": 0, "tiled": 1, "tiled8": 2, "tiled6": 3}[variant]),
+                "dp_set_kernel_variant")
 
     # -- compute ------------------------------------------------------------
     def solve(self, stream=None):

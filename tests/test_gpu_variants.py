@@ -62,12 +62,18 @@ def test_variant_end_to_end_parity(solver, name):
     b.set_variant("direct")
     a.solve()
     b.solve()
+    others = []
+    for variant in ("tiled8", "tiled6"):  # both row counts, whichever the default picks
+        c = solver.EcoDP(p)
+        c.set_variant(variant)
+        c.solve()
+        others.append(c)
     for k in range(p.n_stages, -1, -1):
         gV = a.value(k)
         gp = a.policy(k) if k < p.n_stages else None
-        assert torch.equal(gV, b.value(k))
+        assert torch.equal(gV, b.value(k)) and all(torch.equal(gV, c.value(k)) for c in others)
         if gp is not None:
-            assert torch.equal(gp, b.policy(k))
+            assert torch.equal(gp, b.policy(k)) and all(torch.equal(gp, c.policy(k)) for c in others)
         compare(gV.cpu().numpy(), gp.cpu().numpy() if gp is not None else None, Vn[k], Vl[k], Vh[k],
                 pin[k] if k < p.n_stages else None, secn[k] if k < p.n_stages else None, where=f"{name}/k{k}")
     x0 = feasible_start(p, Vn[0], Vl[0], Vh[0])
@@ -78,6 +84,8 @@ def test_variant_end_to_end_parity(solver, name):
     assert rg["J"] == pytest.approx(ro["J"], rel=1e-3)
     a.close()
     b.close()
+    for c in others:
+        c.close()
 
 
 def test_sampled_indicator_masks_red_nodes_on_gpu(solver):
