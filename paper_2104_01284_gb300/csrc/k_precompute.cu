@@ -140,16 +140,19 @@ __device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, in
 {
     short ord[MAX_MEMBERS];
     int m = 0;
-    for (int ie = mem.ie_lo; ie <= mem.ie_hi && m < MAX_MEMBERS; ++ie) {
+    // insertion by (f desc, cost asc, u asc).  Members arrive in decreasing
+    // engine torque: within a class and shift bucket the SoC fraction f falls
+    // with the motor share, so most arrive already in order (O(1) each)
+    for (int ie = mem.ie_hi; ie >= mem.ie_lo && m < MAX_MEMBERS; --ie) {
         const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
         const CtrlRec r = s_ctrl[u];
         if (!r.ok || r.d != d)
             continue;
-        // insertion by (f desc, cost asc, u asc); members arrive in increasing u
         int q = m++;
         while (q > 0) {
-            const CtrlRec o = s_ctrl[ord[q - 1]];
-            if (o.f > r.f || (o.f == r.f && o.cost <= r.cost))
+            const int ou = ord[q - 1];
+            const CtrlRec o = s_ctrl[ou];
+            if (o.f > r.f || (o.f == r.f && (o.cost < r.cost || (o.cost == r.cost && ou < u))))
                 break;
             ord[q] = ord[q - 1];
             --q;
