@@ -573,9 +573,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     for (int e = e_lo; e < e_hi; ++e) {
         const TileClass T = s_tc[e];
         const ClassEntry E = tile_entry(T, e);
-        const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
         // inner window rows jb - 1 .. jb + R (G[1 .. R + 2]); the outer rows
-        // G[0], G[R + 3] only for the rare buckets d = -2, +1 below
+        // G[0], G[R + 3] only for the rare buckets d = -2, +1 below.  The
+        // second class of a pair needs its interpolation context only there.
         float G[R + 4];
         if (have_h) {
 #pragma unroll
@@ -583,6 +583,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 G[w] = H[w];
             have_h = false;
         } else {
+            const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
             TileClass T2;
             if (can_pair && e + 1 < e_hi) {
                 T2 = s_tc[e + 1];
@@ -624,6 +625,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         // rare (warp-uniform): the outer buckets d = -2, +1 and the lines of
         // any other shift
         if ((E.nb[0] | E.nb[3] | E.n_other) != 0) {
+            const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
             G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
             G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
             Dg[0] = __fsub_rn(G[1], G[0]);
