@@ -624,7 +624,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         }
         // rare (warp-uniform): the outer buckets d = -2, +1 and the lines of
         // any other shift
-        if ((E.nb[0] | E.nb[3] | E.n_other) != 0) {
+        if ((T.nb0 | (int)T.nb3_other) != 0) {  // nb[0], nb[3] or n_other
             const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
             G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
             G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
