@@ -211,7 +211,7 @@ __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const floa
 __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__restrict__ dP, StageTables tb, int k,
                                                             const float *__restrict__ Vn,
                                                             const int16_t *__restrict__ pik,
-                                                            const double *__restrict__ lam_k,
+                                                            double *__restrict__ lam_k,
                                                             double *__restrict__ lam_k1, double *__restrict__ out)
 {
     __shared__ DevParams P;
@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
     if (s < n_states)
         L = lam_k[s];
     if (L != 0.0) {
+        lam_k[s] = 0.0;  // the buffer holds lam_{k+2} next: leave it all zero
         const int u = pik[s];
         const int l = s % P.n_t, j = (s / P.n_t) % P.n_xi, i = s / (P.n_t * P.n_xi);
         DStep st;
@@ -253,7 +254,11 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
             }
         }
     }
-    // FP64 reduction of the gradient: warp, then one atomic per warp
+    // FP64 reduction of the gradient: warp, then one atomic per warp; only
+    // warps that hold part of the support (FP64 arithmetic is slow here, and
+    // the support is a small part of the grid)
+    if (!__any_sync(0xffffffffu, L != 0.0))
+        return;
     for (int q = 0; q < 5; ++q) {
         double x = contrib[q];
         for (int off = 16; off > 0; off >>= 1)
@@ -282,15 +287,14 @@ cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const 
 
 // One stage of the forward lam sweep: lam_{k+1} from lam_k through pi_k and
 // the interpolation weights on J_{k+1} (Vn), with the stage's gradient terms.
+// lam_{k+1}'s half is all zero on entry (cleared by the init, then by the
+// stage that read it two stages earlier).
 cudaError_t launch_adjoint_stage(const DevParams *dP, const DevParams &hP, StageTables tb, int k, const float *Vn,
                                  const int16_t *pik, double *lam, double *out, cudaStream_t s)
 {
     const size_t n = (size_t)hP.n_v * hP.n_xi * hP.n_t;
     double *lk = lam + (size_t)(k & 1) * n;
     double *lk1 = lam + (size_t)((k + 1) & 1) * n;
-    cudaError_t e = cudaMemsetAsync(lk1, 0, n * sizeof(double), s);
-    if (e != cudaSuccess)
-        return e;
     const int blocks = (int)((n + 255) / 256);
     adjoint_stage_kernel<<<blocks, 256, 0, s>>>(dP, tb, k, Vn, pik, lk, lk1, out);
     return cudaGetLastError();
