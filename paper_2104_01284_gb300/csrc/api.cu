@@ -440,8 +440,8 @@ dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h
         dp_status st = recompute_segment(p, c, s);
         if (st != DP_OK)
             return st;
-        DP_CUDA(launch_rollout(p->dP, p->tables(), p->seg_view(c), p->seg_lo(c), p->seg_hi(c), x0[0], x0[1], x0[2],
-                               p->d_roll, p->d_roll_u, s));
+        DP_CUDA(launch_rollout(p->dP, p->hP, p->tables(), p->seg_view(c), p->seg_lo(c), p->seg_hi(c), x0[0], x0[1],
+                               x0[2], p->d_roll, p->d_roll_u, s));
     }
     DP_CUDA(cudaMemcpyAsync(h_out, p->d_roll, roll_doubles(p->N) * sizeof(double), cudaMemcpyDeviceToHost, s));
     DP_CUDA(cudaMemcpyAsync(h_u, p->d_roll_u, (size_t)p->N * sizeof(int), cudaMemcpyDeviceToHost, s));

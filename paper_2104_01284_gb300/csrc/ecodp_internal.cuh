@@ -298,8 +298,9 @@ struct StageView {
 
 // Forward rollout over stages [k_begin, k_end) (a later segment continues from
 // the state left in `out`; see rollout_body).
-cudaError_t launch_rollout(const DevParams *dP, StageTables tb, const StageView &view, int k_begin, int k_end,
-                           double v0, double xi0, double t0, double *out, int *out_u, cudaStream_t s);
+cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const StageView &view,
+                           int k_begin, int k_end, double v0, double xi0, double t0, double *out, int *out_u,
+                           cudaStream_t s);
 
 // ---- batched instances (device descriptors in params[b], inst[b]) ----------
 

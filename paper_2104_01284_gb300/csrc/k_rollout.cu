@@ -139,11 +139,18 @@ struct Cand {
 // [k_begin, k_end).  A later segment continues from the state, fuel, cost and
 // fail stage the previous one left in `out`; the terminal cost is added by
 // the segment that ends at stage N.  CTA rank 0 writes the outputs.
+// Words of the stage tables a rollout stages in shared memory (grade[N],
+// light_of_node[N + 1], cycle / red / offset of each light).
+__host__ __device__ inline int staged_table_words(int N, int n_lights) { return 2 * N + 1 + 3 * n_lights; }
+
 template <int CS>
-__device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables &tb, const StageView &view,
+__device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables &tb_in, const StageView &view,
                              int k_begin, int k_end, double v0, double xi0, double t0, double *__restrict__ out,
-                             int *__restrict__ out_u)
+                             int *__restrict__ out_u, bool stage_tables = false)
 {
+    // the stage tables in shared memory when the launch provides room: each
+    // stage's model step reads them on the critical path of the walk
+    extern __shared__ __align__(16) unsigned char roll_smem[];
     __shared__ DevParams P;
     __shared__ float s_v, s_xi;
     __shared__ double s_t, s_fuel, s_J;
@@ -161,6 +168,28 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
         P = *dP;
     __syncthreads();
     const int N = P.N;
+    StageTables tb = tb_in;
+    if (stage_tables) {
+        float *sg = reinterpret_cast<float *>(roll_smem);
+        int *sl = reinterpret_cast<int *>(sg + N);
+        float *sc = reinterpret_cast<float *>(sl + N + 1);
+        float *sr = sc + P.n_lights, *so = sr + P.n_lights;
+        for (int q = threadIdx.x; q < N; q += blockDim.x)
+            sg[q] = tb_in.grade[q];
+        for (int q = threadIdx.x; q <= N; q += blockDim.x)
+            sl[q] = tb_in.light_of_node[q];
+        for (int q = threadIdx.x; q < P.n_lights; q += blockDim.x) {
+            sc[q] = tb_in.cycle[q];
+            sr[q] = tb_in.red[q];
+            so[q] = tb_in.offset[q];
+        }
+        tb.grade = sg;
+        tb.light_of_node = sl;
+        tb.cycle = sc;
+        tb.red = sr;
+        tb.offset = so;
+        __syncthreads();
+    }
     double *traj = out;
     double *o_dt = out + 3 * (N + 1);
     double *o_wait = o_dt + N;
@@ -320,9 +349,10 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
 
 __global__ void __cluster_dims__(ROLL_CLUSTER, 1, 1) __launch_bounds__(ROLL_THREADS)
     rollout_kernel(const DevParams *__restrict__ dP, StageTables tb, StageView view, int k_begin, int k_end,
-                   double v0, double xi0, double t0, double *__restrict__ out, int *__restrict__ out_u)
+                   double v0, double xi0, double t0, double *__restrict__ out, int *__restrict__ out_u,
+                   bool stage_tables)
 {
-    rollout_body<ROLL_CLUSTER>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
+    rollout_body<ROLL_CLUSTER>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u, stage_tables);
 }
 
 // Batched: one CTA per instance; instance b writes its output block at
@@ -341,10 +371,15 @@ __global__ void __launch_bounds__(ROLL_THREADS)
 
 }  // namespace
 
-cudaError_t launch_rollout(const DevParams *dP, StageTables tb, const StageView &view, int k_begin, int k_end,
-                           double v0, double xi0, double t0, double *out, int *out_u, cudaStream_t s)
+cudaError_t launch_rollout(const DevParams *dP, const DevParams &hP, StageTables tb, const StageView &view,
+                           int k_begin, int k_end, double v0, double xi0, double t0, double *out, int *out_u,
+                           cudaStream_t s)
 {
-    rollout_kernel<<<ROLL_CLUSTER, ROLL_THREADS, 0, s>>>(dP, tb, view, k_begin, k_end, v0, xi0, t0, out, out_u);
+    // stage the tables when they fit in the default 48 KB of shared memory
+    const size_t bytes = (size_t)staged_table_words(hP.N, hP.n_lights) * 4;
+    const bool stage = bytes <= 32 * 1024;
+    rollout_kernel<<<ROLL_CLUSTER, ROLL_THREADS, stage ? bytes : 0, s>>>(dP, tb, view, k_begin, k_end, v0, xi0, t0,
+                                                                         out, out_u, stage);
     return cudaGetLastError();
 }
 
