@@ -20,22 +20,26 @@
 //
 // A tile is one speed row and TLANES lanes; each lane owns one (SoC group of
 // R rows, time node) pair, the pairs of a row laid out back to back so no lane
-// idles on a ragged time axis.  The row's class and line tables are staged in
-// shared memory.  Per class a lane keeps a register window of blended values
-// G and differences D (the outermost two only when a bucket needs them); the
-// lines of a class are grouped by shift d in {-2, -1, 0, 1} so window offsets
-// are compile-time constants; two rows go through one packed FP32 FMA
-// (__ffma2_rn) and two lines through one three-input min.  Only class minima
-// are tracked in the sweep; afterwards each warp buckets its states by
-// winning class in shared memory and re-evaluates that class (bit for bit the
-// same arithmetic) to recover the argmin.  An arrival during red points the
-// class's time corner at the padding columns, so its values come out
-// infeasible without a per-row select.
+// idles on a ragged time axis.  The row's feasible classes (one 32-byte record
+// each) and envelope lines are staged in shared memory.  Per class a lane
+// keeps a register window of blended values G and differences D; the lines
+// of a class are grouped by shift d in {-2, -1, 0, 1} so window offsets are
+// compile-time constants.  The buckets d = -1 and d = 0 take the fast path;
+// the outer buckets (which also need the window's two outer rows) and lines
+// of any other shift sit behind one warp-uniform test per class.  Two rows go
+// through one packed FP32 FMA (__ffma2_rn) and two lines through one
+// three-input min.  Two consecutive classes with the same speed cell and time
+// shift share the loads of their window.  Only class minima are tracked in
+// the sweep; afterwards each warp buckets its states by winning class in
+// shared memory and re-evaluates that class (bit for bit the same arithmetic)
+// to recover the argmin.  An arrival during red points the class's time
+// corner at the padding columns, so its values come out infeasible without a
+// per-row select.
 //
 // Argmin order: (value, torque class, control index).  Among controls with
 // exactly equal FP32 values the first class in class order (brake flag
-// slowest, then total torque ascending) wins, then the lowest control index inside
-// it.  Exact FP32 ties are rounding coincidences of near-equal costs (the
+// slowest, then total torque ascending) wins, then the lowest control index
+// inside it.  Exact FP32 ties are rounding coincidences of near-equal costs (the
 // FP64 recursion has none on the seeded instances); resolving them toward the
 // lowest global control index would re-evaluate every tied class.
 #pragma once
