@@ -18,10 +18,10 @@ using namespace ecodp::host;
 
 namespace ecodp {
 size_t bellman_smem_bytes(const DevParams &hP);
-cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const float *V0, double *lam, double x0,
-                                double xi0, double t0, double *out, cudaStream_t s);
+cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const float *V0, double *lam,
+                                AdjFrontier F, double x0, double xi0, double t0, double *out, cudaStream_t s);
 cudaError_t launch_adjoint_stage(const DevParams *dP, const DevParams &hP, StageTables tb, int k, const float *Vn,
-                                 const int16_t *pik, double *lam, double *out, cudaStream_t s);
+                                 const int16_t *pik, double *lam, AdjFrontier F, double *out, cudaStream_t s);
 
 namespace host {
 
@@ -67,6 +67,14 @@ struct dp_problem {
     int *d_roll_u = nullptr;
     unsigned long long *d_stats = nullptr;
     double *d_lam = nullptr;  // adjoint weights of two consecutive stages
+    int *d_front = nullptr;   // adjoint support lists (AdjFrontier)
+    unsigned *d_fbits = nullptr;
+    int *d_fcnt = nullptr;
+    AdjFrontier frontier() const
+    {
+        const size_t words = (pi_elems + 31) / 32;
+        return AdjFrontier{d_front, d_fbits, d_fcnt, words};
+    }
     double *d_adj = nullptr;  // adjoint output: gradient[5], J_0(x0), error code, flag
 
     HostTables h;  // host copies of the tables (kept until the next update)
@@ -579,6 +587,9 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, (size_t)P.N, &p->d_roll_u));
     TRY(dev_alloc_n(p, (size_t)5, &p->d_stats));
     TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_lam));
+    TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_front));
+    TRY(dev_alloc_n(p, 2 * ((p->pi_elems + 31) / 32), &p->d_fbits));
+    TRY(dev_alloc_n(p, (size_t)3, &p->d_fcnt));
     TRY(dev_alloc_n(p, (size_t)8, &p->d_adj));
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_part));
     TRY(upload_tables(p, p->create_stream));
@@ -868,14 +879,16 @@ dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], do
     if (!p->solved)
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
     cudaStream_t s = (cudaStream_t)stream;
-    DP_CUDA(launch_adjoint_init(p->dP, p->hP, p->Vsweep(0), p->d_lam, x0[0], x0[1], x0[2], p->d_adj, s));
+    DP_CUDA(launch_adjoint_init(p->dP, p->hP, p->Vsweep(0), p->d_lam, p->frontier(), x0[0], x0[1], x0[2], p->d_adj,
+                                s));
     for (int c = 0; c < p->n_segments(); ++c) {
         dp_status st = recompute_segment(p, c, s);
         if (st != DP_OK)
             return st;
         const StageView view = p->seg_view(c);
         for (int k = p->seg_lo(c); k < p->seg_hi(c); ++k)
-            DP_CUDA(launch_adjoint_stage(p->dP, p->hP, p->tables(), k, view.at(k + 1), p->pi(k), p->d_lam, p->d_adj,
+            DP_CUDA(launch_adjoint_stage(p->dP, p->hP, p->tables(), k, view.at(k + 1), p->pi(k), p->d_lam,
+                                         p->frontier(), p->d_adj,
                                          s));
     }
     double h[8];

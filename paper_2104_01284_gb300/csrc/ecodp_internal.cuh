@@ -229,6 +229,17 @@ __device__ __forceinline__ float terminal_cost(const DevParams &P, float v, floa
 
 // ---- launchers (host) -------------------------------------------------------
 
+// The support of the adjoint weights lam_k as explicit lists, so that a stage
+// touches only the states that carry weight: idx[k & 1] lists the states of
+// lam_k (each once: bits[k & 1] marks membership), cnt[k % 3] its length;
+// stage k reads list k, appends to list k + 1 and clears cnt[(k + 2) % 3].
+struct AdjFrontier {
+    int *idx;        // [2][n states]
+    unsigned *bits;  // [2][words(n)]
+    int *cnt;        // [3]
+    size_t words;    // 32-bit words of one membership bitmap
+};
+
 struct StageTables {
     const float *grade;        // [N]
     const int *light_of_node;  // [N+1], -1 = none

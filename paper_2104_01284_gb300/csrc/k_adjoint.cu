@@ -184,11 +184,25 @@ __device__ bool interp_grad(const DevParams &P, const float *__restrict__ V, flo
     return true;
 }
 
-// lam_0 = interpolation weights of x0 on the stage-0 grid; also J_0(x0).
+// Appends state sn to the support list of parity par unless it is listed.
+__device__ __forceinline__ void frontier_add(const AdjFrontier &F, int par, int cnt_slot, size_t n, int sn)
+{
+    const unsigned bit = 1u << (sn & 31);
+    if (atomicOr(F.bits + par * F.words + (sn >> 5), bit) & bit)
+        return;
+    const int pos = atomicAdd(F.cnt + cnt_slot, 1);
+    F.idx[par * n + pos] = sn;
+}
+
+// lam_0 = interpolation weights of x0 on the stage-0 grid (and its support
+// list); also J_0(x0).
 __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const float *__restrict__ V0, double v0,
-                                    double xi0, double t0, double *__restrict__ lam0, double *__restrict__ out)
+                                    double xi0, double t0, double *__restrict__ lam0, AdjFrontier F,
+                                    double *__restrict__ out)
 {
     const DevParams &P = *dP;
+    const size_t n = (size_t)P.n_v * P.n_xi * P.n_t;
+    F.cnt[0] = F.cnt[1] = F.cnt[2] = 0;
     Interp r;
     if (!interp_grad(P, V0, (float)v0, (float)xi0, (float)t0, r)) {
         out[6] = 1.0;  // x0 off the grid
@@ -201,6 +215,7 @@ __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const floa
         const size_t s = (r.corner[q] / P.ld_t / P.xi_rows) * (size_t)P.n_xi * P.n_t +
                          ((r.corner[q] / P.ld_t) % P.xi_rows - 1) * (size_t)P.n_t + r.corner[q] % P.ld_t;
         lam0[s] += (double)r.w[q];
+        frontier_add(F, 0, 0, n, (int)s);
         J += (double)r.w[q] * (double)V0[r.corner[q]];
     }
     out[5] = r.bad ? __longlong_as_double(0x7ff0000000000000LL) : J;
@@ -208,24 +223,37 @@ __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const floa
         out[6] = 2.0;
 }
 
+// Stage k of the forward lam sweep over the support list of lam_k: each
+// listed state re-evaluates its step at the stored argmin, scatters its
+// weight to the successor's corners (listing new ones for stage k + 1),
+// leaves its lam_k entry and list bit at zero for stage k + 2, and adds its
+// gradient terms.
 __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__restrict__ dP, StageTables tb, int k,
                                                             const float *__restrict__ Vn,
                                                             const int16_t *__restrict__ pik,
                                                             double *__restrict__ lam_k,
-                                                            double *__restrict__ lam_k1, double *__restrict__ out)
+                                                            double *__restrict__ lam_k1, AdjFrontier F,
+                                                            double *__restrict__ out)
 {
     __shared__ DevParams P;
     if (threadIdx.x == 0)
         P = *dP;
     __syncthreads();
-    const int n_states = P.n_v * P.n_xi * P.n_t;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double L = 0.0;
+    const size_t n = (size_t)P.n_v * P.n_xi * P.n_t;
+    const int par = k & 1, par1 = (k + 1) & 1;
+    const int n_list = F.cnt[k % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        F.cnt[(k + 2) % 3] = 0;  // read by stage k - 1, appended to by stage k + 1
     double contrib[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (s < n_states)
-        L = lam_k[s];
-    if (L != 0.0) {
-        lam_k[s] = 0.0;  // the buffer holds lam_{k+2} next: leave it all zero
+    bool any = false;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n_list; it += gridDim.x * blockDim.x) {
+        const int s = F.idx[par * n + it];
+        atomicAnd(F.bits + par * F.words + (s >> 5), ~(1u << (s & 31)));
+        const double L = lam_k[s];
+        lam_k[s] = 0.0;
+        if (L == 0.0)
+            continue;
+        any = true;
         const int u = pik[s];
         const int l = s % P.n_t, j = (s / P.n_t) % P.n_xi, i = s / (P.n_t * P.n_xi);
         DStep st;
@@ -234,30 +262,30 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
                                 node_val(P.t_lo, P.t_span, l, P.n_t), u, st) ||
             !interp_grad(P, Vn, st.v1, st.xi1, st.t1, r)) {
             out[6] = 3.0;  // the support reached an infeasible state
-        } else {
-            if (r.bad)
-                out[7] = 1.0;
-            for (int q = 0; q < 5; ++q) {
-                const float term = __fadd_rn(
-                    st.dcost[q],
-                    __fadd_rn(__fmul_rn(r.grad[0], st.dv1[q]),
-                              __fadd_rn(__fmul_rn(r.grad[1], st.dxi1[q]), __fmul_rn(r.grad[2], st.dt1[q]))));
-                contrib[q] = L * (double)term;
-            }
-            for (int q = 0; q < 8; ++q) {
-                if (r.w[q] == 0.f)
-                    continue;
-                const size_t c = r.corner[q];
-                const size_t sn = (c / P.ld_t / P.xi_rows) * (size_t)P.n_xi * P.n_t +
-                                  ((c / P.ld_t) % P.xi_rows - 1) * (size_t)P.n_t + c % P.ld_t;
-                atomicAdd(lam_k1 + sn, L * (double)r.w[q]);
-            }
+            continue;
+        }
+        if (r.bad)
+            out[7] = 1.0;
+        for (int q = 0; q < 5; ++q) {
+            const float term = __fadd_rn(
+                st.dcost[q],
+                __fadd_rn(__fmul_rn(r.grad[0], st.dv1[q]),
+                          __fadd_rn(__fmul_rn(r.grad[1], st.dxi1[q]), __fmul_rn(r.grad[2], st.dt1[q]))));
+            contrib[q] += L * (double)term;
+        }
+        for (int q = 0; q < 8; ++q) {
+            if (r.w[q] == 0.f)
+                continue;
+            const size_t c = r.corner[q];
+            const size_t sn = (c / P.ld_t / P.xi_rows) * (size_t)P.n_xi * P.n_t +
+                              ((c / P.ld_t) % P.xi_rows - 1) * (size_t)P.n_t + c % P.ld_t;
+            atomicAdd(lam_k1 + sn, L * (double)r.w[q]);
+            frontier_add(F, par1, (k + 1) % 3, n, (int)sn);
         }
     }
     // FP64 reduction of the gradient: warp, then one atomic per warp; only
-    // warps that hold part of the support (FP64 arithmetic is slow here, and
-    // the support is a small part of the grid)
-    if (!__any_sync(0xffffffffu, L != 0.0))
+    // warps that held part of the support (FP64 arithmetic is slow here)
+    if (!__any_sync(0xffffffffu, any))
         return;
     for (int q = 0; q < 5; ++q) {
         double x = contrib[q];
@@ -270,9 +298,10 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
 
 }  // namespace
 
-// lam_0 from x0 and J_0(x0) (out[5]); clears the gradient and both lam halves.
-cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const float *V0, double *lam, double x0,
-                                double xi0, double t0, double *out, cudaStream_t s)
+// lam_0 from x0 and J_0(x0) (out[5]); clears the gradient, both lam halves
+// and both support bitmaps.
+cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const float *V0, double *lam,
+                                AdjFrontier F, double x0, double xi0, double t0, double *out, cudaStream_t s)
 {
     const size_t n = (size_t)hP.n_v * hP.n_xi * hP.n_t;
     cudaError_t e = cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
@@ -281,22 +310,32 @@ cudaError_t launch_adjoint_init(const DevParams *dP, const DevParams &hP, const 
     e = cudaMemsetAsync(lam, 0, 2 * n * sizeof(double), s);
     if (e != cudaSuccess)
         return e;
-    adjoint_init_kernel<<<1, 1, 0, s>>>(dP, V0, x0, xi0, t0, lam, out);
+    e = cudaMemsetAsync(F.bits, 0, 2 * F.words * sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    adjoint_init_kernel<<<1, 1, 0, s>>>(dP, V0, x0, xi0, t0, lam, F, out);
     return cudaGetLastError();
 }
 
 // One stage of the forward lam sweep: lam_{k+1} from lam_k through pi_k and
 // the interpolation weights on J_{k+1} (Vn), with the stage's gradient terms.
-// lam_{k+1}'s half is all zero on entry (cleared by the init, then by the
-// stage that read it two stages earlier).
+// lam_{k+1}'s half and its bitmap are all zero on entry (cleared by the init,
+// then by the stage that read them two stages earlier).  A fixed grid walks
+// the support list, whose length only the device knows.
 cudaError_t launch_adjoint_stage(const DevParams *dP, const DevParams &hP, StageTables tb, int k, const float *Vn,
-                                 const int16_t *pik, double *lam, double *out, cudaStream_t s)
+                                 const int16_t *pik, double *lam, AdjFrontier F, double *out, cudaStream_t s)
 {
     const size_t n = (size_t)hP.n_v * hP.n_xi * hP.n_t;
     double *lk = lam + (size_t)(k & 1) * n;
     double *lk1 = lam + (size_t)((k + 1) & 1) * n;
-    const int blocks = (int)((n + 255) / 256);
-    adjoint_stage_kernel<<<blocks, 256, 0, s>>>(dP, tb, k, Vn, pik, lk, lk1, out);
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    adjoint_stage_kernel<<<4 * sms, 256, 0, s>>>(dP, tb, k, Vn, pik, lk, lk1, F, out);
     return cudaGetLastError();
 }
 
