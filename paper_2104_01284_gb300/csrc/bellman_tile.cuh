@@ -57,12 +57,18 @@ constexpr int TLANES = TW * 32;
 
 // Loads of J_{k+1}: through the read-only path when J_{k+1} cannot change
 // during the launch (one stage per launch), through L1/L2 otherwise (a
-// persistent launch whose other CTAs wrote it, ordered by an acquire).
+// persistent launch whose other CTAs wrote it, ordered by an acquire).  The
+// read-only loads ask L1 to evict these lines last: consecutive classes read
+// nearly the same cells of J_{k+1}, while the row's tables sit in shared
+// memory.
 template <bool NC>
 __device__ __forceinline__ float ldv(const float *p)
 {
-    if (NC)
-        return __ldg(p);
+    if (NC) {
+        float v;
+        asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
     return __ldca(p);
 }
 
