@@ -442,6 +442,21 @@ __device__ __forceinline__ TCtx tile_ctx(const DevParams &P, const float *Vn, co
         l, tl, wait, si);
 }
 
+// A 32-byte table record read with the streaming (evict-first) hint: it is
+// staged in shared memory once per tile and must not crowd J_{k+1} out of L1.
+template <class T>
+__device__ __forceinline__ T ld_stream(const T *p)
+{
+    static_assert(sizeof(T) == 32, "32-byte records");
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+    const int4 a = __ldcs(q), b = __ldcs(q + 1);
+    T t;
+    int4 *d = reinterpret_cast<int4 *>(&t);
+    d[0] = a;
+    d[1] = b;
+    return t;
+}
+
 // Shared memory of a tile: the row's feasible classes (TileClass, then the
 // flagged step times) and lines as {c, f} (a line outside the four buckets
 // reads its shift, and argmin recovery its control index, from the global
@@ -524,15 +539,13 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             }
         }
         for (int q = c_lo + tid; q < c_hi; q += TLANES) {
-            const ClassEntry E = g_ent[q];
-            const ClassRec C = g_cls[E.cls];
+            const ClassEntry E = ld_stream(g_ent + q);
+            const ClassRec C = ld_stream(g_cls + E.cls);
             s_tc[q] = tile_class(C, E);
             s_dtv[q] = dt_flagged(C);
         }
-        for (int q = q_lo + tid; q < q_hi; q += TLANES) {
-            const SplitRec S = g_spl[q];
-            s_line[q] = make_float2(S.c, S.f);
-        }
+        for (int q = q_lo + tid; q < q_hi; q += TLANES)
+            s_line[q] = __ldcs(reinterpret_cast<const float2 *>(g_spl + q));
     }
     const int warp = tid >> 5, lane = tid & 31;
     unsigned char *wbase = smem_raw + L.warp + warp * L.warp_bytes;
