@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 # of this workload) from an ncu capture of the current kernel version; see
 # profiles/bellman_tiled_c1_stage79.md.  Reset to None whenever the kernel
 # changes until it is captured again.
-BELLMAN_TRAFFIC_BYTES = 3.732224e6
+BELLMAN_TRAFFIC_BYTES = 3.732992e6
 
 
 def parse():
