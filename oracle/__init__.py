@@ -13,6 +13,7 @@ Entry points (see ecodp_oracle.c for the semantics and the paper passages):
   rollout(op, Vall, x0)
   model_step(op, k, v, soc, t, Te, Tm, b)
   sequence_cost(op, x0, useq)
+  evaluate(op, k, Vnext, v, soc, t, ie, im, b, mode)
 """
 from __future__ import annotations
 
@@ -95,6 +96,9 @@ def lib():
             L.orc_sequence_cost.argtypes = [P, vp, vp, vp]
             L.orc_sequence_cost.restype = C.c_double
             L.orc_adjoint.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_eval.argtypes = [P, C.c_int, C.c_int, vp, C.c_double, C.c_double, C.c_double,
+                                   C.c_int, C.c_int, C.c_int, vp]
+            L.orc_eval.restype = C.c_double
             _lib = L
     return _lib
 
@@ -280,12 +284,12 @@ def adjoint(op: OracleProblem, x0=None):
         raise RuntimeError("call solve(op) first")
     x0 = np.array(op.p.x0 if x0 is None else x0, np.float64)
     grad = np.zeros(5)
-    diag = np.zeros(4)
+    diag = np.zeros(6)
     support = np.zeros(op._Vall.size, np.uint8)
     rc = lib().orc_adjoint(op.ref, _ptr(op._Vall), _ptr(op._piall), _ptr(op._secall), _ptr(x0), _ptr(grad),
                            _ptr(diag), _ptr(support))
     d = dict(support_size=int(diag[0]), snapped=bool(diag[1]), infeasible_corner=bool(diag[2]),
-             min_gap=float(diag[3]))
+             min_gap=float(diag[3]), near_tie_mass=float(diag[4]), snapped_mass=float(diag[5]))
     return grad, d, support, int(rc)
 
 
@@ -298,6 +302,18 @@ def model_step(op: OracleProblem, k, v, soc, t, Te, Tm, b):
     if not ok:
         return None
     return dict(zip(("v1", "soc1", "t1", "dt", "wait", "fuel_rate", "cost"), out.tolist()))
+
+
+def evaluate(op: OracleProblem, k, Vnext, v, soc, t, ie, im, b, mode: int = NOMINAL):
+    """One transition's value c + J_{k+1}(f(x, u)) from the stage-k state
+    (v, soc, t) under control (ie, im, b) in a mode; returns (value, number of
+    fragile decisions met by the nominal evaluation)."""
+    Vn = np.ascontiguousarray(Vnext, np.float64)
+    assert Vn.shape == op.shapes[k + 1]
+    nf = np.zeros(1, np.int32)
+    F = lib().orc_eval(op.ref, int(k), int(mode), _ptr(Vn), float(v), float(soc), float(t), int(ie), int(im),
+                       int(b), _ptr(nf))
+    return float(F), int(nf[0])
 
 
 def terminal_cost(op: OracleProblem, v, soc) -> float:

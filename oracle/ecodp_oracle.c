@@ -494,6 +494,20 @@ int orc_model_step(const orc_problem *P, int k, double v, double xi, double t, d
     return ok;
 }
 
+/* One transition's value c + J_{k+1}(f(x, u)) in a mode (the quantity the
+ * backward step minimises, Eq. 9b), for tests of the fragile-decision
+ * bookkeeping; *nfrag receives the number of fragile decisions met by the
+ * nominal evaluation (may be NULL). */
+double orc_eval(const orc_problem *P, int k, int mode, const double *Vnext, double v, double xi, double t,
+                int ie, int im, int b, int32_t *nfrag)
+{
+    int nf = 0;
+    double F = eval_mode(P, k, Vnext, v, xi, t, ie, im, b, mode, 0, &nf, NULL);
+    if (nfrag)
+        *nfrag = nf;
+    return F;
+}
+
 /* Interpolate a stage value array at a point (nominal decisions). */
 double orc_interp(const orc_problem *P, int stage, const double *V, double v, double xi, double t)
 {
@@ -803,11 +817,15 @@ static int interp_grad(const orc_problem *P, int stage, const double *V, double 
 }
 
 /* Forward lambda sweep.  Vall, piall as filled by orc_solve (nominal).
- * grad[5] receives dJ_0(x0)/dtheta.  diag[4]: number of (stage, state) pairs
+ * grad[5] receives dJ_0(x0)/dtheta.  diag[6]: number of (stage, state) pairs
  * on the lambda support, 1 if a snapped fraction was met on the support, 1 if
  * an infeasible corner entered a value or gradient, the smallest relative gap
  * (second - best) / |best| of the policy on the support (needs secall, else
- * NaN).  support (optional, [total states of stages 0..N-1]) receives the
+ * NaN), the lambda mass (summed over stages; each stage carries mass 1) on
+ * support states whose relative gap is at most 1e-4 (needs secall, else
+ * NaN), and the lambda mass on support states whose successor met a snapped
+ * fraction.  The two masses bound how much of the gradient rests on
+ * decisions that a lower-precision solver may take differently.  support (optional, [total states of stages 0..N-1]) receives the
  * support as 0/1 flags.  Returns ORC_ERR_INFEASIBLE if the support reaches an
  * infeasible state. */
 int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, const double *secall,
@@ -823,6 +841,8 @@ int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, 
     diag[1] = 0;
     diag[2] = 0;
     diag[3] = secall ? INFINITY : NAN;
+    diag[4] = secall ? 0.0 : NAN;
+    diag[5] = 0.0;
     /* lambda_0: interpolation weights of x0 on the stage-0 grid */
     {
         int64_t cn[8];
@@ -863,6 +883,8 @@ int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, 
                 double gap = (secall[base + s] - best) / fabs(best);
                 if (gap < diag[3])
                     diag[3] = gap;
+                if (!(gap > 1e-4))
+                    diag[4] += L;
             }
             int i = (int)(s / ((int64_t)nx * nt)), j = (int)((s / nt) % nx), l = (int)(s % nt);
             int bb = u % P->n_b, im = (u / P->n_b) % P->n_tm, ie = u / (P->n_b * P->n_tm);
@@ -882,8 +904,10 @@ int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, 
             }
             if (rc == 2)
                 diag[2] = 1;
-            if (sn)
+            if (sn) {
                 diag[1] = 1;
+                diag[5] += L;
+            }
             for (int q = 0; q < 5; ++q)
                 grad[q] += L * (dg.dcost[q] + gr[0] * dg.dv1[q] + gr[1] * dg.dxi1[q] + gr[2] * dg.dt1[q]);
             for (int q = 0; q < 8; ++q)
