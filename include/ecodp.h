@@ -197,9 +197,10 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
  *   pi_out:  pi_k, int16 same shape, DEVICE memory (caller-owned)
  * Results equal those of dp_solve_stage on the same inputs.  Limits: n_v <= 64,
  * n_soc <= 64, n_t <= 255, at most 2048 controls and 256 torque classes;
- * larger problems get DP_ERR_INVALID_ARG.  Asynchronous on stream.  The first
- * call on each device looks up the array's device address (a set-up step);
- * make that first call before capturing any stream into a CUDA graph.  Every
+ * larger problems get DP_ERR_INVALID_ARG.  Asynchronous on stream.  Each call
+ * looks up the array's address on the current device; the first call on a
+ * device also loads the library's device code there (a set-up step), so make
+ * that first call before any stream capture begins.  Every
  * call on a device shares that device's one array, so calls whose GPU work
  * can overlap (issued on different streams or from different host threads)
  * race and corrupt each other's results: order them on one stream.  Each

@@ -7,7 +7,6 @@
 #include <cstdlib>
 #include <cstddef>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -937,8 +936,34 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
 // Its working memory is one file-scope device array, sized for the limits
 // below and resident on every GPU that loads this library until the process
 // exits.  Host code must not pass the array's name to a kernel (on the host
-// it only stands in for the symbol); each device's address is looked up once
-// with cudaGetSymbolAddress and cached.
+// it only stands in for the symbol); every call looks up the current device's
+// address of the array with cudaGetSymbolAddress (a host-side lookup; after a
+// device reset the module is reloaded and the address may change, so it is
+// not cached).
+
+// The stage's own route tables, re-indexed as stage 0 of a one-stage
+// problem: grade, light index at the departure node (0) and at the arrival
+// node (1), and those lights' timings.  (Outside the anonymous namespace: it
+// appears in a kernel's signature.)
+struct StaticTables {
+    float grade[4];
+    int lon[2];
+    float cyc[2], red[2], off[2];
+};
+
+// Stores one call's parameters and stage tables into the static array.  They
+// travel as kernel arguments, so no host buffer has to outlive the call and
+// no host-to-device copy is issued.  (In a named namespace: nvcc's launch
+// stubs cannot name a kernel of this file's second anonymous namespace.)
+namespace stage_static {
+__global__ void static_setup_kernel(DevParams P, StaticTables t, DevParams *dP, StaticTables *dT)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *dP = P;
+        *dT = t;
+    }
+}
+}  // namespace stage_static
 
 namespace {
 
@@ -950,7 +975,7 @@ constexpr size_t STATIC_PAD_ELEMS = (size_t)STATIC_MAX_V * (STATIC_MAX_SOC + 2) 
 constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t ST_OFF_PARAMS = 0;
 constexpr size_t ST_OFF_TABLES = ST_OFF_PARAMS + a256(sizeof(DevParams));
-constexpr size_t ST_TABLE_BYTES = a256(4 * sizeof(float) + 2 * sizeof(int) + 6 * sizeof(float));
+constexpr size_t ST_TABLE_BYTES = a256(sizeof(StaticTables));
 constexpr size_t ST_OFF_CLS = ST_OFF_TABLES + ST_TABLE_BYTES;
 constexpr size_t ST_OFF_ENT = ST_OFF_CLS + a256((size_t)STATIC_MAX_V * STATIC_MAX_CLS * sizeof(ClassRec));
 constexpr size_t ST_OFF_ROWCNT = ST_OFF_ENT + a256((size_t)STATIC_MAX_V * STATIC_MAX_CLS * sizeof(ClassEntry));
@@ -961,25 +986,14 @@ constexpr size_t ST_BYTES = ST_OFF_PAD_OUT + a256(STATIC_PAD_ELEMS * sizeof(floa
 
 __device__ __align__(256) unsigned char g_stage_scratch[ST_BYTES];
 
-std::mutex g_static_mu;
-void *g_static_addr[128] = {};
-
-// Device address of g_stage_scratch on the current device (set-up on first use).
+// Device address of g_stage_scratch on the current device.
 dp_status static_scratch(unsigned char **out)
 {
-    int dev = -1;
-    DP_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128)
-        return fail(DP_ERR_CUDA, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_stage_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(DP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_static_addr[dev] = ptr;
-    }
-    *out = (unsigned char *)g_static_addr[dev];
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_stage_scratch);
+    if (e != cudaSuccess || !ptr)
+        return fail(DP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = (unsigned char *)ptr;
     return DP_OK;
 }
 
@@ -1008,13 +1022,7 @@ extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t 
         return st;
     cudaStream_t s = (cudaStream_t)stream;
 
-    // the stage's own tables, re-indexed as stage 0 of a one-stage problem:
-    // grade, light index at the departure node (0) and at the arrival node (1)
-    struct {
-        float grade[4];
-        int lon[2];
-        float cyc[2], red[2], off[2];
-    } tbl = {};
+    StaticTables tbl = {};
     tbl.grade[0] = (float)desc->grade[k];
     tbl.lon[0] = tbl.lon[1] = -1;
     tbl.cyc[0] = tbl.cyc[1] = 1.f;
@@ -1028,14 +1036,14 @@ extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t 
             }
         }
     }
-    static_assert(sizeof(tbl) <= ST_TABLE_BYTES, "table block");
-    unsigned char *tb_dev = base + ST_OFF_TABLES;
+    StaticTables *tb_dev = (StaticTables *)(base + ST_OFF_TABLES);
     DevParams *dP = (DevParams *)(base + ST_OFF_PARAMS);
-    StageTables tb{(const float *)(tb_dev + offsetof(decltype(tbl), grade)),
-                   (const int *)(tb_dev + offsetof(decltype(tbl), lon)),
-                   (const float *)(tb_dev + offsetof(decltype(tbl), cyc)),
-                   (const float *)(tb_dev + offsetof(decltype(tbl), red)),
-                   (const float *)(tb_dev + offsetof(decltype(tbl), off))};
+    unsigned char *tb_bytes = base + ST_OFF_TABLES;
+    StageTables tb{(const float *)(tb_bytes + offsetof(StaticTables, grade)),
+                   (const int *)(tb_bytes + offsetof(StaticTables, lon)),
+                   (const float *)(tb_bytes + offsetof(StaticTables, cyc)),
+                   (const float *)(tb_bytes + offsetof(StaticTables, red)),
+                   (const float *)(tb_bytes + offsetof(StaticTables, off))};
     StageScratch sc{(ClassRec *)(base + ST_OFF_CLS), (ClassEntry *)(base + ST_OFF_ENT), (int *)(base + ST_OFF_ROWCNT),
                     (SplitRec *)(base + ST_OFF_SPL), nullptr, nullptr};
     if (P.ld_t > (int)STATIC_LD_T || (size_t)P.n_v * P.xi_rows * P.ld_t > STATIC_PAD_ELEMS)
@@ -1044,8 +1052,8 @@ extern "C" dp_status dp_solve_stage_static(const dp_problem_desc *desc, int32_t 
     float *pad_out = (float *)(base + ST_OFF_PAD_OUT);
     const size_t pad_elems = (size_t)P.n_v * P.xi_rows * P.ld_t;
 
-    DP_CUDA(cudaMemcpyAsync(dP, &P, sizeof P, cudaMemcpyHostToDevice, s));
-    DP_CUDA(cudaMemcpyAsync(tb_dev, &tbl, sizeof tbl, cudaMemcpyHostToDevice, s));
+    stage_static::static_setup_kernel<<<1, 32, 0, s>>>(P, tbl, dP, tb_dev);
+    DP_CUDA(cudaGetLastError());
     // the padding of J_{k+1} must read as infeasible: refill it every call,
     // since the array keeps whatever the previous call left there
     DP_CUDA(launch_fill(pad_in, pad_elems, V_BIG, s));

@@ -447,7 +447,7 @@ __device__ __forceinline__ TCtx tile_ctx(const DevParams &P, const float *Vn, co
 template <class T>
 __device__ __forceinline__ T ld_stream(const T *p)
 {
-    static_assert(sizeof(T) == 32, "32-byte records");
+    static_assert(sizeof(T) == 32 && alignof(T) >= 16, "32-byte records on 16-byte boundaries");
     const int4 *q = reinterpret_cast<const int4 *>(p);
     const int4 a = __ldcs(q), b = __ldcs(q + 1);
     T t;

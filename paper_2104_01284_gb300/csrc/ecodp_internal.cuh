@@ -71,7 +71,7 @@ __device__ __forceinline__ bool torque_allowed(const DevParams &P, float w, floa
 // A torque class: all controls with the same total torque T_eng + T_bsg and
 // brake flag share the speed update (Eq. 5a) and the step time (Eq. 2), hence
 // the speed-axis and time-axis interpolation of J_{k+1}.
-struct ClassRec {
+struct __align__(16) ClassRec {
     int ok;     // feasible at class level (Eq. 7a, 7d, stopping rule)
     int iv;     // lower speed node of v'
     float fv;   // snapped weight of node iv + 1
@@ -93,7 +93,7 @@ struct __align__(16) SplitRec {
     unsigned pad;
 };
 
-struct ClassEntry {
+struct __align__(16) ClassEntry {
     int cls;    // class index
     int off;    // first split record of this class in the row's split array
     int nb[4];  // lower-envelope controls with soc shift d = -2, -1, 0, +1

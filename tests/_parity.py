@@ -73,7 +73,8 @@ def compare(gpu_V, gpu_pi, nom, lo, hi, pi_nom=None, second=None, rtol=RTOL, ato
     n_feas = int(fn.sum())
     stats = dict(where=where, states=int(gV.size), feasible=n_feas, mask_exceptions=int(excused.sum()),
                  loose=int((fn & ~tight).sum()), value_checked=int(tight.sum()),
-                 max_rel_err=float(np.max(err[tight] / np.abs(nom[tight]))) if tight.any() else 0.0)
+                 max_rel_err=float(np.max(np.where(err[tight] == 0, 0.0, err[tight] / np.abs(nom[tight]))))
+                 if tight.any() else 0.0)
     # (c) policy
     if gpu_pi is not None and pi_nom is not None and second is not None:
         gp = np.asarray(gpu_pi).astype(np.int64)

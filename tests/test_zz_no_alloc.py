@@ -20,14 +20,27 @@ pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore")]
 torch = pytest.importorskip("torch")
 
 
-def _problem():
-    # several SoC tiles and time warps with ragged tails; lights with short
-    # cycles so arrival and departure rules are exercised
-    p = P.config1(seed=41, n_stages=8, n_v=21, n_soc=19, n_t=45, n_te=11, n_tm=11, n_lights=3)
-    rng = np.random.Generator(np.random.PCG64(41))
+def _short_cycles(p, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
     n = len(p.light_stage)
     cyc = rng.uniform(6.0, 14.0, n)
     return p.replace(cycle=cyc, red=cyc * rng.uniform(0.3, 0.6, n), offset=rng.uniform(0, 1, n) * cyc)
+
+
+PROBLEMS = {
+    # several SoC tiles and time warps with ragged tails; lights with short
+    # cycles so arrival and departure rules are exercised
+    "ragged": lambda: _short_cycles(P.config1(seed=41, n_stages=8, n_v=21, n_soc=19, n_t=45, n_te=11, n_tm=11,
+                                              n_lights=3), 41),
+    # every documented limit at once: 64 speeds, 64 SoC points, 255 times,
+    # 32 x 32 x 2 = 2048 controls (126 torque classes)
+    "limits": lambda: P.config1(seed=42, n_stages=6, n_v=64, n_soc=64, n_t=255, n_te=32, n_tm=32, n_lights=2),
+    # the literal standstill step (light_model 2) with speed-dependent torque
+    # limits (torque_limits 1)
+    "variants": lambda: _short_cycles(P.config1(seed=43, n_stages=8, n_v=21, n_soc=19, n_t=45, n_te=9, n_tm=11,
+                                                n_lights=3), 43).replace(
+        light_model=2, torque_limits=1, te_max_coef=np.array([110.0, 0.9, -0.003]), bsg_power_max=6500.0),
+}
 
 
 def _same(a_v, a_pi, b_v, b_pi):
@@ -38,13 +51,14 @@ def _same(a_v, a_pi, b_v, b_pi):
     assert torch.equal(a_pi, b_pi)
 
 
-def test_static_stage_matches_allocating_stage_twice():
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_static_stage_matches_allocating_stage_twice(name):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2104_01284_gb300.native as N
     from paper_2104_01284_gb300.solver import EcoDP, make_desc
 
-    p = _problem()
+    p = PROBLEMS[name]()
     dev = torch.device("cuda", 0)
     dp = EcoDP(p, device=dev)
     desc, keep = make_desc(p)
