@@ -33,13 +33,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DP state x control evals/s (ms per horizon solve)"
 UNIT = "evals/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
+FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample exists
 # dram__bytes_read.sum + dram__bytes_write.sum of one Bellman launch (stage 79
-# of this workload) from an ncu capture of the current kernel version; see
-# profiles/bellman_tiled_c1_stage79.md.  Reset to None whenever the kernel
-# changes until it is captured again.
+# of this workload) from an ncu capture of the current kernel version (ncu's
+# counters cannot be read inside a timed run).  None whenever the kernel has
+# changed since the last capture.
 BELLMAN_TRAFFIC_BYTES = 3.732992e6
 
 
@@ -120,10 +119,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(p, target_s, seed=11):
+def cpu_baseline(p, target_s, seed=11, single_s=4.0):
     """Time the FP64 oracle (as it stands) on the host cores on a bounded
     sample: one Bellman stage of the same instance evaluated at a seeded
-    random subset of states, every control at each."""
+    random subset of states, every control at each; on every core, and on
+    one core (the analogue of the paper's serial solver column)."""
     import numpy as np
 
     import oracle as O
@@ -132,19 +132,28 @@ def cpu_baseline(p, target_s, seed=11):
     k = p.n_stages // 2
     Vn = P.synthetic_value_field(p, seed=seed)
     rng = np.random.Generator(np.random.PCG64(seed))
-    probe = rng.choice(p.n_states, size=2000, replace=False)
-    t0 = time.perf_counter()
-    O.stage(op, k, Vn, idx=probe)
-    rate = probe.size / max(1e-6, time.perf_counter() - t0)
-    n = int(min(p.n_states, max(2000, rate * target_s)))
-    idx = rng.choice(p.n_states, size=n, replace=False)
-    t0 = time.perf_counter()
-    O.stage(op, k, Vn, idx=idx)
-    dt = time.perf_counter() - t0
-    evals = n * p.n_controls
-    return {"value": evals / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    cores = os.cpu_count()
+
+    def timed(n_target_s, nthreads):
+        probe = rng.choice(p.n_states, size=1000 if nthreads == 1 else 2000, replace=False)
+        t0 = time.perf_counter()
+        O.stage(op, k, Vn, idx=probe, nthreads=nthreads)
+        rate = probe.size / max(1e-6, time.perf_counter() - t0)
+        n = int(min(p.n_states, max(500, rate * n_target_s)))
+        idx = rng.choice(p.n_states, size=n, replace=False)
+        t0 = time.perf_counter()
+        O.stage(op, k, Vn, idx=idx, nthreads=nthreads)
+        return n, time.perf_counter() - t0
+
+    n, dt = timed(target_s, cores)
+    n1, dt1 = timed(single_s, 1)
+    evals, evals1 = n * p.n_controls, n1 * p.n_controls
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one Bellman stage (k={k}) of the bench instance at {n} random states x "
-                      f"{p.n_controls} controls = {evals:.3e} evals in {dt:.1f} s, FP64, OpenMP"}
+                      f"{p.n_controls} controls = {evals:.3e} evals in {dt:.1f} s, FP64, OpenMP",
+            "single_core": {"value": evals1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} random states of the same stage, {evals1:.3e} evals in {dt1:.1f} s",
+                            "ms_per_solve_equiv": 1e3 * p.evals_per_solve / (evals1 / dt1)}}
 
 
 def dist_setup(args):
@@ -314,9 +323,49 @@ def bench_serving(dev, seconds):
         run_fleet(srv, fleet, rate_rps=500.0, duration_s=0.2, seed=96)
         single["saturation"] = run_fleet(srv, fleet, rate_rps=2000.0, duration_s=seconds, seed=1)
         single["half_saturation"] = run_fleet(srv, fleet, rate_rps=half, duration_s=seconds, seed=int(half))
+    import torch
+    stream = torch.cuda.Stream(dev)
+    persistent = {n: bench_fleet_persistent(dev, stream, n_req=n) for n in (8, 16, 32)}
     return {"workload": "1000 vehicles, 5 km routes, 10 lights; 50-stage horizon 51x51x101 states x 1922 controls",
             "saturation_solves_per_s_by_slots": sat, "slots": best, "runs": runs,
-            "one_at_a_time": single, "deadline_s": 1.0, "slot_stats": stats}
+            "one_at_a_time": single, "deadline_s": 1.0, "slot_stats": stats,
+            "persistent_batch_by_requests": persistent}
+
+
+def bench_fleet_persistent(dev, stream, n_req=16, steps=3):
+    """The serving workload's requests through the persistent batched kernel
+    instead of per-slot streams: n_req fleet horizon problems (50 stages,
+    51 x 51 x 101 states, 1922 controls) solved as one batch (terminal,
+    precompute and one persistent Bellman launch under a CUDA graph, tile
+    configuration autotuned), then rolled out; solves/s of the whole
+    (backward sweeps and rollouts), for comparison with the serving loop's
+    saturation throughput."""
+    import torch
+
+    from paper_2104_01284_gb300.serving import Fleet
+    from paper_2104_01284_gb300.solver import EcoDPBatch
+    fleet = Fleet(n_vehicles=n_req)
+    reqs = [fleet.request(v) for v in range(n_req)]
+    probs = [p for p, _ in reqs]
+    x0 = [x for _, x in reqs]
+    with torch.cuda.stream(stream):
+        bt = EcoDPBatch(probs, device=dev, stream=stream)
+        best = bt.autotune(repeats=1, stream=stream)
+        bt.set_config(best["rows_per_lane"], best["ctas_per_sm"])
+        bt.solve(stream)
+        bt.rollout(x0=x0, stream=stream, raise_infeasible=False)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            bt.solve(stream)
+            bt.rollout(x0=x0, stream=stream, raise_infeasible=False)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        bt.close()
+    s = statistics.median(times)
+    return {"requests": n_req, "solves_per_s": n_req / s, "ms_per_batch": 1e3 * s,
+            "tile_config": {"rows_per_lane": best["rows_per_lane"], "ctas_per_sm": best["ctas_per_sm"]}}
 
 
 def bench_paper_grid(dev, stream, reps=20):
@@ -347,6 +396,33 @@ def bench_paper_grid(dev, stream, reps=20):
             "ms_per_solve_p99": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
             "nominal_evals_per_s": p.evals_per_solve / (ms / 1e3),
             "paper_context_ms": {"rtx2080_parallel_mean": 98, "cpu_serial_mean": 1600}}
+
+
+ROOFLINE_KEYS = ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic", "peak_basis",
+                 "bellman_ms_per_launch", "share_of_sweep")
+
+
+def headline(adjoint, paper_grid, batched, serving):
+    """Compact numbers of the adjoint, the paper's Table I grid, the
+    256-instance batch and the serving loop."""
+    h = {"adjoint_ms_per_call": adjoint["ms_per_call"],
+         "paper_grid_ms_per_solve": paper_grid["ms_per_solve_median"]}
+    if batched:
+        h["batched"] = {"instances": batched["instances"], "solves_per_s": batched["solves_per_s"],
+                        "single_path_solves_per_s": batched["single_path_solves_per_s"],
+                        "speedup_vs_single_path": batched["speedup_vs_single_path"]}
+    if serving:
+        half = serving["runs"]["half_saturation"]
+        one = serving["one_at_a_time"]
+        h["serving"] = {"slots": serving["slots"],
+                        "saturation_solves_per_s": serving["saturation_solves_per_s_by_slots"][serving["slots"]],
+                        "one_at_a_time_solves_per_s": one["saturation"]["solves_per_s"],
+                        "half_saturation_rps": half["offered_rps"], "p50_ms": half["p50_ms"], "p99_ms": half["p99_ms"],
+                        "one_at_a_time_p50_ms": one["half_saturation"]["p50_ms"],
+                        "one_at_a_time_p99_ms": one["half_saturation"]["p99_ms"],
+                        "persistent_batch_solves_per_s": {n: r["solves_per_s"] for n, r in
+                                                          serving["persistent_batch_by_requests"].items()}}
+    return h
 
 
 def run_ours(args):
@@ -408,11 +484,16 @@ def run_ours(args):
     # two-way blends of J_{k+1} (9 FLOP), the SoC-row difference and the add
     flops_per_launch = (2.0 * stats["envelope_evals"] + 11.0 * stats["class_evals"]) / p.n_stages
     achieved = flops_per_launch / per_launch_s / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # FP32 FMA peak from the device's SM count and the SM clock sampled
+    # during the timed region
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or FALLBACK_SM_MHZ
+    peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "bellman_tiled", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": BELLMAN_TRAFFIC_BYTES,
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts)",
+                "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {mhz:.0f} MHz "
+                              f"({'median sampled SM clock' if clocks.get('sm_mhz') else 'maximum SM clock'})",
                 "work_basis": "2 FLOP per (state, envelope line) FMA + 11 FLOP per (state, torque class) window value",
                 "bellman_ms_per_launch": 1e3 * per_launch_s,
                 "share_of_sweep": bell_ms / sweep_ms if sweep_ms > 0 else None,
@@ -472,12 +553,17 @@ def run_ours(args):
         "ms_per_solve_p99": float(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))]),
         "rollout": {"fuel_g": traj["fuel_g"], "time_s": traj["time_s"], "J": traj["J"]},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks, "adjoint": adjoint, "paper_grid": paper_grid, "batched": batched,
-        "serving": serving,
+        "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    # the other workloads' headline numbers on the JSON line; their full
+    # records (per offered load, tile configuration, ...) go to stderr first
+    line["headline"] = headline(adjoint, paper_grid, batched, serving)
     if rank == 0:
+        print(json.dumps({"details": {"adjoint": adjoint, "paper_grid": paper_grid, "batched": batched,
+                                      "serving": serving, "roofline": roofline}}), file=sys.stderr, flush=True)
+        line["roofline"] = {k: v for k, v in roofline.items() if k in ROOFLINE_KEYS}
         print(json.dumps(line), flush=True)
     dp.close()
     if world > 1:

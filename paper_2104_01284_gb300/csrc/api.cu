@@ -718,6 +718,7 @@ dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant)
 
 dp_status dp_solve_backward(dp_problem_t p, void *stream)
 {
+    NvtxRange nvtx_("ecodp.sweep");
     if (!p)
         return fail(DP_ERR_INVALID_ARG, "problem is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -754,6 +755,7 @@ dp_status dp_solve_backward(dp_problem_t p, void *stream)
 
 dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
 {
+    NvtxRange nvtx_("ecodp.profile_sweep");
     if (!p || !ms)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -770,6 +772,7 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
         DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, N, p->scratch(), s));
         DP_CUDA(cudaEventRecord(ev[2], s));
         for (int k = N - 1, q = 3; k >= 0; --k, ++q) {
+            NvtxRange stage_range(("ecodp.stage " + std::to_string(k)).c_str());
             DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
                                    p->variant, s));
             DP_CUDA(cudaEventRecord(ev[q], s));
@@ -871,6 +874,7 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
 
 dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream)
 {
+    NvtxRange nvtx_("ecodp.adjoint");
     if (!p || !x0 || !dJ_dtheta)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!finite_all({x0[0], x0[1], x0[2]}))
@@ -906,6 +910,7 @@ dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], do
 
 dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream)
 {
+    NvtxRange nvtx_("ecodp.rollout");
     if (!p || !x0 || !traj)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!traj->v || !traj->soc || !traj->t || !traj->u || !traj->dt || !traj->wait || !traj->fuel)

@@ -2,6 +2,8 @@
 // single problems, api_multi.cu for batches and the serving loop).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
@@ -34,6 +36,15 @@ struct HostTables {
 void fill_tables(const dp_problem_desc *d, HostTables &t);
 
 bool finite3(const double x[3]);
+
+// An NVTX range over a scope (host timeline; a profiler projects it onto the
+// GPU work launched inside).  No effect unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+    ~NvtxRange() { nvtxRangePop(); }
+};
 const char *last_error();
 
 // Single-problem helpers (api.cu) for the batch and serving entry points.

@@ -372,6 +372,7 @@ dp_status dp_multi_set_config(dp_multi_t m, int32_t rows_per_lane, int32_t ctas_
 
 dp_status dp_multi_solve(dp_multi_t m, void *stream)
 {
+    NvtxRange nvtx_("ecodp.batch.solve");
     if (!m)
         return fail(DP_ERR_INVALID_ARG, "batch is NULL");
     cudaStream_t s = (cudaStream_t)stream;

@@ -135,6 +135,7 @@ dp_status dp_batch_destroy(dp_batch_t b)
 
 dp_status dp_batch_submit(dp_batch_t b, const dp_problem_desc *desc, const double x0[3], uint64_t *ticket)
 {
+    NvtxRange nvtx_("ecodp.serve.admit");
     if (!b || !desc || !x0 || !ticket)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     dp_status st = validate(desc);

@@ -337,11 +337,13 @@ def config4_fleet(seed: int = 4, n_vehicles: int = 1000, route_m: float = 5000.0
 
 
 def horizon_problem(fuel: np.ndarray, route, start_node: int, t0: float,
-                    n_stages: int = 50, n_t: int = 101, name: str = "c4") -> Problem:
+                    n_stages: int = 50, n_t: int = 101, name: str = "c4", n_v: int = 51, n_soc: int = 51,
+                    n_te: int = 31, n_tm: int = 31) -> Problem:
     """The receding-horizon window [start_node, start_node + n_stages) of a
     route as a stand-alone problem whose time grid starts at t0 (absolute
     route time), as in config 4: grids as config 1 but 101 time points over
-    the window's 2 s/step budget."""
+    the window's 2 s/step budget.  The keyword sizes shrink the grids for
+    tests while keeping the structure."""
     grade, nodes, cyc, red, off = route
     g = np.asarray(grade)[start_node:start_node + n_stages]
     if g.size < n_stages:
@@ -350,9 +352,9 @@ def horizon_problem(fuel: np.ndarray, route, start_node: int, t0: float,
     keep = (rel >= 1) & (rel <= n_stages - 1)
     return Problem(
         name=name, n_stages=n_stages, ds=10.0, grade=g,
-        v_lo=0.0, v_hi=25.0, n_v=51, soc_lo=0.30, soc_hi=0.80, n_soc=51,
+        v_lo=0.0, v_hi=25.0, n_v=n_v, soc_lo=0.30, soc_hi=0.80, n_soc=n_soc,
         t_lo=float(t0), t_hi=float(t0) + 2.0 * n_stages, n_t=n_t,
-        te_lo=0.0, te_hi=200.0, n_te=31, tm_lo=-100.0, tm_hi=100.0, n_tm=31,
+        te_lo=0.0, te_hi=200.0, n_te=n_te, tm_lo=-100.0, tm_hi=100.0, n_tm=n_tm,
         n_brake=2, fuel_coef=np.array(fuel, copy=True),
         light_stage=rel[keep].astype(np.int32), cycle=cyc[keep], red=red[keep],
         offset=off[keep])

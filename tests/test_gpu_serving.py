@@ -1,10 +1,11 @@
 """Serving (continuous batching of receding-horizon re-solves) through the
-C ABI (needs a GB300): each request's result is the same alone and in the
-mix, slots are re-used in place, admission respects the memory budget, and
-the open-loop fleet driver runs."""
+C ABI (needs a GB300): each request's result matches the FP64 oracle and is
+the same alone and in the mix, slots are re-used in place, admission
+respects the memory budget, and the open-loop fleet driver runs."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2104_01284_gb300 import problems as P
 
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore")]
@@ -32,6 +33,73 @@ def fleet_requests(n, seed=4):
         p = P.horizon_problem(fuel, routes[v], node, t0)
         out.append((p, (10.0, 0.55, t0)))
     return out
+
+
+REDUCED = dict(n_stages=12, n_t=45, n_v=21, n_soc=19, n_te=11, n_tm=11)
+
+
+def fleet_requests_with_lights(n, seed=4):
+    """n reduced horizon problems of the config-4 fleet (12 stages, 21 x 19 x
+    45 states, 11 x 11 x 2 controls), each window placed so that one of its
+    vehicle's lights falls 2-10 steps ahead, with start times spread over
+    the lights' cycles."""
+    fuel, routes = P.config4_fleet(seed=seed, n_vehicles=n)
+    rng = np.random.Generator(np.random.PCG64(seed + 2))
+    out = []
+    for v in range(n):
+        nodes = routes[v][1]
+        j = int(rng.integers(0, len(nodes)))
+        node = max(0, int(nodes[j]) - int(rng.integers(2, 11)))
+        t0 = float(rng.uniform(0.0, 300.0))
+        out.append((P.horizon_problem(fuel, routes[v], node, t0, **REDUCED), (10.0, 0.55, t0)))
+    return out
+
+
+def serve_all(srv, reqs):
+    """Submit every request as slots free up, collecting results as they
+    finish (requests overlap on the device)."""
+    tickets, results, pending = {}, {}, list(range(len(reqs)))
+    while pending or tickets:
+        while pending:
+            t = srv.submit(*reqs[pending[0]])
+            if t is None:
+                break
+            tickets[t] = pending.pop(0)
+        for t in list(tickets):
+            r = srv.poll(t)
+            if r is not None:
+                results[tickets.pop(t)] = r
+    return results
+
+
+def test_served_results_match_the_oracle(mods):
+    """Twelve fleet-shaped requests (receding-horizon windows with a light
+    ahead, Sec. III Eq. 6 and the MPC loop of Sec. V) served three at a time:
+    each result's feasibility equals the oracle's wherever the oracle's three
+    modes agree on it, and a feasible result's fuel, time and cost are within
+    0.1 % of the oracle's rollout from the same start (acceptance (d))."""
+    serving, _ = mods
+    import paper_2104_01284_gb300.native as N
+    reqs = fleet_requests_with_lights(12)
+    assert sum(len(p.light_stage) > 0 for p, _ in reqs) >= 10
+    with serving.EcoDPServer(max_slots=3, mem_budget_bytes=8 << 30) as srv:
+        results = serve_all(srv, reqs)
+    n_feasible = 0
+    for i, (p, x0) in enumerate(reqs):
+        op = O.make(p)
+        Vn, _, _ = O.solve(op, O.NOMINAL)
+        ro = O.rollout(op, Vn, x0)
+        j0 = [O.interp(op, 0, O.solve(op, m)[0][0], *x0) for m in (O.LENIENT, O.STRICT)]
+        robust = np.isfinite(j0[0]) == np.isfinite(j0[1])
+        r = results[i]
+        if robust:
+            assert (r["status"] == N.DP_OK) == (ro["status"] == 0), (i, r["status"], ro["status"])
+        if ro["status"] == 0 and r["status"] == N.DP_OK:
+            n_feasible += 1
+            assert r["fuel_g"] == pytest.approx(ro["fuel_g"], rel=1e-3, abs=1e-6), i
+            assert r["time_s"] == pytest.approx(ro["time_s"], rel=1e-3), i
+            assert r["J"] == pytest.approx(ro["J"], rel=1e-3), i
+    assert n_feasible >= 6
 
 
 def same(a, b):
