@@ -180,6 +180,25 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
  * control (traj->fail_stage tells which); DP_ERR_NOT_SOLVED before a solve. */
 dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream);
 
+/* Bounds-check report (a debugging aid; no counterpart in the paper).  The
+ * library ships in two builds from the same sources: libecodp.so and the
+ * bounds-checked libecodp_checked.so, in which every index the kernels
+ * compute into shared or global memory is compared with its array's extent
+ * before the access.  A failed check never traps: the kernel records the
+ * first failure (source tag, line, index) in a device word, skips the
+ * access and goes on, and the host reports it as DP_ERR_INTERNAL.
+ *   enabled: (host, may be NULL) 1 in the checked build, 0 otherwise; set
+ *            without touching the device
+ *   site:    (host, may be NULL) receives the first recorded failure
+ *            (tag << 48 | line << 32 | index), 0 if none; the record is then
+ *            cleared.  Reading it synchronises the device.
+ * Returns DP_ERR_INTERNAL (with the site in dp_last_error) when a failure was
+ * recorded, DP_OK otherwise (always in the production build).  In the
+ * checked build dp_rollout, dp_adjoint, dp_multi_wait, dp_multi_rollout and a
+ * completed dp_batch_poll check the record themselves and return
+ * DP_ERR_INTERNAL instead of their result when it is set. */
+dp_status dp_debug_checks(int32_t *enabled, uint64_t *site);
+
 /* One stage of the recursion, like dp_solve_stage, for callers that cannot
  * allocate GPU memory.  The paper has no counterpart; this entry point exists
  * for integrations whose memory is fixed after start-up: a controller task

@@ -281,6 +281,19 @@ void fill_tables(const dp_problem_desc *d, HostTables &t)
 
 bool finite3(const double x[3]) { return finite_all({x[0], x[1], x[2]}); }
 
+dp_status checks_after(dp_status st)
+{
+#ifdef ECODP_CHECKS
+    if (st != DP_OK && st != DP_ERR_INFEASIBLE)
+        return st;
+    uint64_t site = 0;
+    const dp_status c = dp_debug_checks(nullptr, &site);
+    if (c != DP_OK)
+        return c;
+#endif
+    return st;
+}
+
 }  // namespace host
 }  // namespace ecodp
 
@@ -872,9 +885,8 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
     return DP_OK;
 }
 
-dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream)
+static dp_status adjoint_impl(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream)
 {
-    NvtxRange nvtx_("ecodp.adjoint");
     if (!p || !x0 || !dJ_dtheta)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!finite_all({x0[0], x0[1], x0[2]}))
@@ -908,9 +920,8 @@ dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], do
     return DP_OK;
 }
 
-dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream)
+static dp_status rollout_impl(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream)
 {
-    NvtxRange nvtx_("ecodp.rollout");
     if (!p || !x0 || !traj)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!traj->v || !traj->soc || !traj->t || !traj->u || !traj->dt || !traj->wait || !traj->fuel)
@@ -930,6 +941,50 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
     const int fail_stage = unpack_rollout(N, h.data(), hu.data(), traj);
     if (fail_stage >= 0)
         return fail(DP_ERR_INFEASIBLE, "no feasible control at stage " + std::to_string(fail_stage));
+    return DP_OK;
+}
+
+dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream)
+{
+    NvtxRange nvtx_("ecodp.rollout");
+    return checks_after(rollout_impl(p, x0, traj, stream));
+}
+
+dp_status dp_adjoint(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream)
+{
+    NvtxRange nvtx_("ecodp.adjoint");
+    return checks_after(adjoint_impl(p, x0, dJ_dtheta, J0, stream));
+}
+
+dp_status dp_debug_checks(int32_t *enabled, uint64_t *site)
+{
+#ifdef ECODP_CHECKS
+    if (enabled)
+        *enabled = 1;
+#else
+    if (enabled)
+        *enabled = 0;
+#endif
+    if (!site)
+        return DP_OK;
+    *site = 0;
+#ifdef ECODP_CHECKS
+    DP_CUDA(cudaDeviceSynchronize());
+    cudaError_t (*const words[])(unsigned long long *) = {check_word_precompute, check_word_bellman,
+                                                          check_word_rollout, check_word_adjoint, check_word_batch};
+    for (auto fn : words) {
+        unsigned long long w = 0;
+        DP_CUDA(fn(&w));
+        if (w && !*site)
+            *site = w;
+    }
+    if (*site) {
+        const unsigned tag_line = (unsigned)(*site >> 32);
+        return fail(DP_ERR_INTERNAL, "bounds check failed in kernel source " + std::to_string(tag_line >> 16) +
+                                         " at line " + std::to_string(tag_line & 0xffffu) + ", index " +
+                                         std::to_string((int)(unsigned)(*site & 0xffffffffu)));
+    }
+#endif
     return DP_OK;
 }
 

@@ -37,6 +37,11 @@ void fill_tables(const dp_problem_desc *d, HostTables &t);
 
 bool finite3(const double x[3]);
 
+// In the bounds-checked build: after a call that synchronised with the
+// device, a recorded bounds failure turns st (DP_OK or DP_ERR_INFEASIBLE)
+// into DP_ERR_INTERNAL.  The production build returns st unchanged.
+dp_status checks_after(dp_status st);
+
 // An NVTX range over a scope (host timeline; a profiler projects it onto the
 // GPU work launched inside).  No effect unless a tool is attached.
 struct NvtxRange {

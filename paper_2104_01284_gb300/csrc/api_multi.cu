@@ -404,7 +404,7 @@ dp_status dp_multi_wait(dp_multi_t m, void *stream)
 {
     if (!m)
         return fail(DP_ERR_INVALID_ARG, "batch is NULL");
-    return check_error_flag(m, (cudaStream_t)stream);
+    return checks_after(check_error_flag(m, (cudaStream_t)stream));
 }
 
 dp_status dp_multi_profile(dp_multi_t m, void *stream, float ms[3])
@@ -553,7 +553,7 @@ dp_status dp_multi_get_policy(dp_multi_t m, int32_t b, int32_t stage, int16_t *o
     return check_error_flag(m, s);
 }
 
-dp_status dp_multi_rollout(dp_multi_t m, const double *x0, dp_trajectory *traj, void *stream)
+static dp_status multi_rollout_impl(dp_multi_t m, const double *x0, dp_trajectory *traj, void *stream)
 {
     if (!m || !x0 || !traj)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
@@ -587,6 +587,11 @@ dp_status dp_multi_rollout(dp_multi_t m, const double *x0, dp_trajectory *traj, 
         return fail(DP_ERR_INFEASIBLE, "instance " + std::to_string(first_fail) + ": no feasible control at stage " +
                                            std::to_string(traj[first_fail].fail_stage));
     return DP_OK;
+}
+
+dp_status dp_multi_rollout(dp_multi_t m, const double *x0, dp_trajectory *traj, void *stream)
+{
+    return checks_after(multi_rollout_impl(m, x0, traj, stream));
 }
 
 }  // extern "C"

@@ -237,8 +237,8 @@ dp_status dp_batch_poll(dp_batch_t b, uint64_t ticket, dp_trajectory *traj)
     b->inflight.erase(it);
     ++b->completed;
     if (fail_stage >= 0)
-        return fail(DP_ERR_INFEASIBLE, "no feasible control at stage " + std::to_string(fail_stage));
-    return DP_OK;
+        return checks_after(fail(DP_ERR_INFEASIBLE, "no feasible control at stage " + std::to_string(fail_stage)));
+    return checks_after(DP_OK);
 }
 
 dp_status dp_batch_stats(dp_batch_t b, int64_t out[8])

@@ -48,6 +48,9 @@
 
 #include "ecodp_internal.cuh"
 
+#undef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 6
+
 namespace ecodp {
 namespace tile {
 
@@ -142,7 +145,13 @@ __device__ __forceinline__ TCtx class_ctx_at(const DevParams &P, const float *Vn
         red = true;
     // a lower corner past the grid reads the padding column n_t; the upper
     // corner is the next column, still inside the row (ld_t >= n_t + 2)
-    const int ta = red ? P.n_t : min(t0, P.n_t);
+    int ta = red ? P.n_t : min(t0, P.n_t);
+    // the window reads speed rows iv, iv + 1 and time columns ta, ta + 1 of
+    // every padded SoC row
+    if (!DP_IN(iv, P.n_v - 1) || !DP_IN(ta, P.ld_t - 1)) {
+        iv = 0;
+        ta = P.n_t;
+    }
     x.wt1 = ft;
     x.wt0 = __fsub_rn(1.f, ft);
     x.wv1 = fv;
@@ -539,13 +548,18 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             }
         }
         for (int q = c_lo + tid; q < c_hi; q += TLANES) {
+            if (!DP_IN(q, P.n_cls))
+                break;
             const ClassEntry E = ld_stream(g_ent + q);
+            if (!DP_IN(E.cls, P.n_cls) || !DP_IN(E.off, P.n_u + 1) || !DP_IN((long long)E.off + E.n_total, P.n_u + 1))
+                continue;
             const ClassRec C = ld_stream(g_cls + E.cls);
             s_tc[q] = tile_class(C, E);
             s_dtv[q] = dt_flagged(C);
         }
         for (int q = q_lo + tid; q < q_hi; q += TLANES)
-            s_line[q] = __ldcs(reinterpret_cast<const float2 *>(g_spl + q));
+            if (DP_IN(q, P.n_u))
+                s_line[q] = __ldcs(reinterpret_cast<const float2 *>(g_spl + q));
     }
     const int warp = tid >> 5, lane = tid & 31;
     unsigned char *wbase = smem_raw + L.warp + warp * L.warp_bytes;
@@ -594,8 +608,13 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     float H[R + 4];
     bool have_h = false;
     for (int e = e_lo; e < e_hi; ++e) {
+        if (!DP_IN(e, P.n_cls))
+            break;
         const TileClass T = s_tc[e];
         const ClassEntry E = tile_entry(T, e);
+        if (!DP_IN(E.off, P.n_u + 1) ||
+            !DP_IN((long long)E.off + E.nb[0] + E.nb[1] + E.nb[2] + E.nb[3] + E.n_other, P.n_u + 1))
+            continue;
         // inner window rows jb - 1 .. jb + R (G[1 .. R + 2]); the outer rows
         // G[0], G[R + 3] only for the rare buckets d = -2, +1 below.  The
         // second class of a pair needs its interpolation context only there.
@@ -688,8 +707,10 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int j = jb + r;
-            if (f_ok && j < P.n_xi && best[r] < __int_as_float(0x7f800000))
-                atomicMin(part + ((size_t)i * P.n_xi + j) * P.n_t + l, pack_min(best[r], bcls[r]));
+            const size_t o = ((size_t)i * P.n_xi + j) * P.n_t + l;
+            if (f_ok && j < P.n_xi && best[r] < __int_as_float(0x7f800000) &&
+                DP_IN(o, (size_t)P.n_v * P.n_xi * P.n_t))
+                atomicMin(part + o, pack_min(best[r], bcls[r]));
         }
         return;
     }
@@ -703,11 +724,12 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const bool feas = valid && !masked && best[r] < V_FEAS_MAX;
         if (feas)
             todo |= 1u << r;
-        if (valid) {
-            Vk[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] =
-                feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
+        const size_t ov = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
+        const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + l;
+        if (valid && DP_IN(ov, (size_t)P.n_v * P.xi_rows * P.ld_t) && DP_IN(op, (size_t)P.n_v * P.n_xi * P.n_t)) {
+            Vk[ov] = feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
             if (!feas)
-                pik[((size_t)i * P.n_xi + j) * P.n_t + l] = -1;
+                pik[op] = -1;
         }
     }
     if (stats) {
@@ -719,11 +741,12 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     // bucket the feasible states by their first winning class and recover the
     // lowest winning control of that class, warp-wide class by class
     for (int q = lane; q < n_ent; q += 32)
-        w_cnt[q] = 0;
+        if (DP_IN(q, P.n_cls + 1))
+            w_cnt[q] = 0;
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if ((todo >> r) & 1u) {
+        if (((todo >> r) & 1u) && DP_IN(bcls[r], n_ent)) {
             atomicAdd(&w_cnt[bcls[r]], 1);
             w_best[lane * R + r] = best[r];
         }
@@ -747,17 +770,22 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if ((todo >> r) & 1u) {
+        if (((todo >> r) & 1u) && DP_IN(bcls[r], n_ent)) {
             const int key = bcls[r];
             const int pos = atomicAdd(&w_cnt[key], 1);
-            w_list[pos] = ((unsigned)key << 16) | (unsigned)(lane * R + r);
+            if (DP_IN(pos, 32 * R))
+                w_list[pos] = ((unsigned)key << 16) | (unsigned)(lane * R + r);
         }
     }
     __syncwarp();
     for (int q = lane; q < total; q += 32) {
+        if (!DP_IN(q, 32 * R))
+            break;
         const unsigned en = w_list[q];
         const int e = (int)(en >> 16);
         const int s = (int)(en & 0xffffu);
+        if (!DP_IN(e, n_ent) || !DP_IN(s, 32 * R))
+            continue;
         const int ln = s / R, r = s - ln * R;
         const int fq = chunk0 + ln;
         const int jgq = fq / P.n_t;
@@ -768,8 +796,9 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const ClassEntry E = tile_entry(T, e);
         const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, lq, tlq, wq, si);
         const int j = jgq * R + r;
-        pik[((size_t)i * P.n_xi + j) * P.n_t + lq] =
-            (int16_t)class_lowest_u<NC>(P, x, E, s_line, g_spl, j, w_best[s]);
+        const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + lq;
+        if (DP_IN(op, (size_t)P.n_v * P.n_xi * P.n_t))
+            pik[op] = (int16_t)class_lowest_u<NC>(P, x, E, s_line, g_spl, j, w_best[s]);
     }
 }
 

@@ -28,7 +28,59 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Bounds-checked build (compiled with -DECODP_CHECKS into a second library,
+// libecodp_checked.so).  Every index a kernel computes into shared or global
+// memory is compared with its array's extent before the access, through
+// DP_IN(index, extent).  A failed check records the first failure -- the
+// source file's tag (ECODP_FILE_TAG, set per file), the line and the index --
+// in the translation unit's device word, skips the access (the code takes a
+// safe fallback) and never traps; the host reads the words and reports
+// DP_ERR_INTERNAL.  In the production build DP_IN is the constant true and
+// costs nothing.
+#ifndef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 0
+#endif
+
 namespace ecodp {
+
+#ifdef ECODP_CHECKS
+static __device__ unsigned long long g_check_word;  // one per translation unit
+
+__device__ __forceinline__ bool dp_in_range(long long i, long long n, unsigned line, unsigned tag)
+{
+    if (i >= 0 && i < n)
+        return true;
+    const unsigned long long site = ((unsigned long long)((tag << 16) | (line & 0xffffu)) << 32) | (unsigned)i;
+    atomicCAS(&g_check_word, 0ull, site);
+    return false;
+}
+#define DP_IN(i, n) ::ecodp::dp_in_range((long long)(i), (long long)(n), __LINE__, ECODP_FILE_TAG)
+// Host: this translation unit's word (first failure, 0 if none), then cleared.
+#define ECODP_CHECK_ACCESSOR(name)                                                       \
+    cudaError_t name(unsigned long long *w)                                              \
+    {                                                                                    \
+        cudaError_t e = cudaMemcpyFromSymbol(w, g_check_word, sizeof *w);                \
+        if (e != cudaSuccess || *w == 0)                                                 \
+            return e;                                                                    \
+        const unsigned long long zero = 0;                                               \
+        return cudaMemcpyToSymbol(g_check_word, &zero, sizeof zero);                     \
+    }
+#else
+#define DP_IN(i, n) true
+#define ECODP_CHECK_ACCESSOR(name)          \
+    cudaError_t name(unsigned long long *w) \
+    {                                       \
+        *w = 0;                             \
+        return cudaSuccess;                 \
+    }
+#endif
+
+// the check words of the kernel translation units (all 0 in the production build)
+cudaError_t check_word_precompute(unsigned long long *w);
+cudaError_t check_word_bellman(unsigned long long *w);
+cudaError_t check_word_rollout(unsigned long long *w);
+cudaError_t check_word_adjoint(unsigned long long *w);
+cudaError_t check_word_batch(unsigned long long *w);
 
 constexpr float V_BIG = 1e30f;
 constexpr float V_FEAS_MAX = 1e12f;

@@ -11,7 +11,12 @@
 // in FP64.
 #include "ecodp_internal.cuh"
 
+#undef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 4
+
 namespace ecodp {
+
+ECODP_CHECK_ACCESSOR(check_word_adjoint)
 
 namespace {
 
@@ -33,7 +38,9 @@ __device__ bool step_grad(const DevParams &P, const StageTables &tb, int k, floa
     const float cos_th = __fdiv_rn(1.f, sq);
     const float F_road = road_load(P, v, __fdiv_rn(p, sq), cos_th);
     const int nl = tb.light_of_node[k + 1];
-    const int lk = tb.light_of_node[k];
+    int lk = tb.light_of_node[k];
+    if (!DP_IN(lk + 1, P.n_lights + 1))
+        lk = -1;
     if (P.light_model == 2 && lk >= 0 && v == 0.f) {
         // literal Eq. 5c at the line: the zero-speed step has no theta
         // dependence (v' = 0, SoC kept, time jump to the end of red)
@@ -151,6 +158,10 @@ __device__ bool interp_grad(const DevParams &P, const float *__restrict__ V, flo
         r.corner[q] = ((size_t)(iv + a) * P.xi_rows + (ix + b + 1)) * P.ld_t + (it + c);
         r.w[q] = __fmul_rn(__fmul_rn(a ? fv : __fsub_rn(1.f, fv), b ? fx : __fsub_rn(1.f, fx)),
                            c ? ft : __fsub_rn(1.f, ft));
+        if (!DP_IN(r.corner[q], (size_t)P.n_v * P.xi_rows * P.ld_t)) {
+            r.corner[q] = 0;
+            r.w[q] = 0.f;
+        }
         val[q] = V[r.corner[q]];
         if (r.w[q] != 0.f && !(val[q] < V_FEAS_MAX))
             r.bad = true;
@@ -188,10 +199,11 @@ __device__ bool interp_grad(const DevParams &P, const float *__restrict__ V, flo
 __device__ __forceinline__ void frontier_add(const AdjFrontier &F, int par, int cnt_slot, size_t n, int sn)
 {
     const unsigned bit = 1u << (sn & 31);
-    if (atomicOr(F.bits + par * F.words + (sn >> 5), bit) & bit)
+    if (!DP_IN(sn, n) || (atomicOr(F.bits + par * F.words + (sn >> 5), bit) & bit))
         return;
     const int pos = atomicAdd(F.cnt + cnt_slot, 1);
-    F.idx[par * n + pos] = sn;
+    if (DP_IN(pos, n))
+        F.idx[par * n + pos] = sn;
 }
 
 // lam_0 = interpolation weights of x0 on the stage-0 grid (and its support
@@ -214,6 +226,8 @@ __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const floa
             continue;
         const size_t s = (r.corner[q] / P.ld_t / P.xi_rows) * (size_t)P.n_xi * P.n_t +
                          ((r.corner[q] / P.ld_t) % P.xi_rows - 1) * (size_t)P.n_t + r.corner[q] % P.ld_t;
+        if (!DP_IN(s, n))
+            continue;
         lam0[s] += (double)r.w[q];
         frontier_add(F, 0, 0, n, (int)s);
         J += (double)r.w[q] * (double)V0[r.corner[q]];
@@ -247,7 +261,11 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
     double contrib[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     bool any = false;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n_list; it += gridDim.x * blockDim.x) {
+        if (!DP_IN(it, n))
+            break;
         const int s = F.idx[par * n + it];
+        if (!DP_IN(s, n))
+            continue;
         atomicAnd(F.bits + par * F.words + (s >> 5), ~(1u << (s & 31)));
         const double L = lam_k[s];
         lam_k[s] = 0.0;
@@ -279,6 +297,8 @@ __global__ void __launch_bounds__(256) adjoint_stage_kernel(const DevParams *__r
             const size_t c = r.corner[q];
             const size_t sn = (c / P.ld_t / P.xi_rows) * (size_t)P.n_xi * P.n_t +
                               ((c / P.ld_t) % P.xi_rows - 1) * (size_t)P.n_t + c % P.ld_t;
+            if (!DP_IN(sn, n))
+                continue;
             atomicAdd(lam_k1 + sn, L * (double)r.w[q]);
             frontier_add(F, par1, (k + 1) % 3, n, (int)sn);
         }

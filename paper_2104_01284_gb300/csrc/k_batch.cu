@@ -13,7 +13,12 @@
 // waits cannot deadlock whatever the number of resident CTAs.
 #include "bellman_tile.cuh"
 
+#undef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 5
+
 namespace ecodp {
+
+ECODP_CHECK_ACCESSOR(check_word_batch)
 
 namespace {
 
@@ -70,9 +75,13 @@ __global__ void __launch_bounds__(TLANES, MINB) bellman_persistent(const DevPara
             const long long item = (long long)atomicAdd(S.queue, 1ull);
             s_item = item;
             if (item < S.n_items) {
-                const int j = upper_bound_idx(S.start, S.max_n + 1, item) - 1;
+                int j = upper_bound_idx(S.start, S.max_n + 1, item) - 1;
+                if (!DP_IN(j, S.max_n))
+                    j = 0;
                 const long long r = item - S.start[j];
-                const int rank = upper_bound_idx(S.pref, S.m[j] + 1, r) - 1;
+                int rank = upper_bound_idx(S.pref, S.m[j] + 1, r) - 1;
+                if (!DP_IN(rank, S.m[j]))
+                    rank = 0;
                 s_j = j;
                 s_b = S.order[rank];
                 s_tile = (int)(r - S.pref[rank]);
@@ -93,6 +102,10 @@ __global__ void __launch_bounds__(TLANES, MINB) bellman_persistent(const DevPara
         const int k = I.N - 1 - s_j;
         const int i = s_tile / I.chunks;
         const int chunk = s_tile - i * I.chunks;
+        if (!DP_IN(k, I.N) || !DP_IN(s_tile, I.tiles) || !DP_IN(i, P.n_v)) {
+            __syncthreads();
+            continue;  // uniform over the CTA (shared item); the stage's counter is left short
+        }
         if (k + 1 < I.N) {  // stage k + 1 must be complete (stage N is the terminal cost)
             if (threadIdx.x == 0) {
                 const unsigned long long t0 = global_ns();

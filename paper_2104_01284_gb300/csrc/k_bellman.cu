@@ -10,7 +10,12 @@
 
 #include "bellman_tile.cuh"
 
+#undef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 2
+
 namespace ecodp {
+
+ECODP_CHECK_ACCESSOR(check_word_bellman)
 
 namespace {
 
@@ -40,6 +45,8 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     const StageInfo si = stage_info(tb, k, v);
     const float wait = wait_time(tb, k, tl, si.wait_row);
     const size_t row = (size_t)k * P.n_v + i;
+    if (!DP_IN(row, (size_t)P.N * P.n_v))
+        return;
     const int n_ent = sc.row_cnt[2 * row];
     const ClassRec *cls = sc.cls + row * P.n_cls;
     const ClassEntry *ent = sc.ent + row * P.n_cls;
@@ -49,7 +56,11 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     float best = __int_as_float(0x7f800000);
     int bu = INT_MAX, be = -1;
     for (int e = 0; e < n_ent; ++e) {
+        if (!DP_IN(e, P.n_cls))
+            break;
         const ClassEntry E = ent[e];
+        if (!DP_IN(E.cls, P.n_cls) || !DP_IN(E.off, P.n_u + 1) || !DP_IN((long long)E.off + E.n_total, P.n_u + 1))
+            continue;
         const TCtx x = class_ctx(P, Vn, cls[E.cls], l, tl, wait, si);
         for (int q = E.off; q < E.off + E.n_total; ++q) {
             const SplitRec S = spl[q];
@@ -145,8 +156,10 @@ __global__ void __launch_bounds__(256) bellman_join(const DevParams *__restrict_
         const unsigned long long w = sc.part[op];
         sc.part[op] = ~0ull;
         const float best = w != ~0ull ? __uint_as_float((unsigned)(w >> 32)) : __int_as_float(0x7f800000);
-        if (best < V_FEAS_MAX && !sampled_red(P, tb, si, v, tl)) {
-            const ClassEntry E = sc.ent[row * P.n_cls + (int)(unsigned)(w & 0xffffffffu)];
+        const int we = (int)(unsigned)(w & 0xffffffffu);
+        if (best < V_FEAS_MAX && !sampled_red(P, tb, si, v, tl) && DP_IN(we, sc.row_cnt[2 * row]) &&
+            DP_IN(row, (size_t)P.N * P.n_v)) {
+            const ClassEntry E = sc.ent[row * P.n_cls + we];
             const TCtx x = class_ctx(P, Vn, sc.cls[row * P.n_cls + E.cls], l, tl, wait, si);
             Vk[o] = __fadd_rn(best, __fmul_rn(__fsub_rn(1.f, P.gamma), wait));
             pik[op] = (int16_t)class_lowest_u_global<true>(P, x, E, sc.spl + row * P.n_u, j, best);

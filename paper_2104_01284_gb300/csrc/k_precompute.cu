@@ -16,7 +16,12 @@
 // only reads those results back from shared memory.
 #include "ecodp_internal.cuh"
 
+#undef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 1
+
 namespace ecodp {
+
+ECODP_CHECK_ACCESSOR(check_word_precompute)
 
 namespace {
 
@@ -36,7 +41,9 @@ __global__ void terminal_kernel(const DevParams *__restrict__ dP, float *__restr
         int i = s / (P.n_t * P.n_xi);
         float v = node_val(P.v_lo, P.v_span, i, P.n_v);
         float xi = node_val(P.xi_lo, P.xi_span, j, P.n_xi);
-        VN[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] = terminal_cost(P, v, xi);
+        const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
+        if (DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t))
+            VN[o] = terminal_cost(P, v, xi);
     }
 }
 
@@ -48,7 +55,9 @@ __global__ void pad_from_dense_kernel(const DevParams P, const float *__restrict
         int j = (s / P.n_t) % P.n_xi;
         int i = s / (P.n_t * P.n_xi);
         float x = dense[s];
-        padded[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] = (x < V_FEAS_MAX) ? x : V_BIG;
+        const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
+        if (DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t))
+            padded[o] = (x < V_FEAS_MAX) ? x : V_BIG;
     }
 }
 
@@ -59,7 +68,8 @@ __global__ void dense_from_pad_kernel(const DevParams P, const float *__restrict
         int l = s % P.n_t;
         int j = (s / P.n_t) % P.n_xi;
         int i = s / (P.n_t * P.n_xi);
-        float x = padded[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l];
+        const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
+        float x = DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t) ? padded[o] : V_BIG;
         dense[s] = (x < V_FEAS_MAX) ? x : __int_as_float(0x7f800000);
     }
 }
@@ -145,6 +155,8 @@ __device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, in
     // with the motor share, so most arrive already in order (O(1) each)
     for (int ie = mem.ie_hi; ie >= mem.ie_lo && m < MAX_MEMBERS; --ie) {
         const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
+        if (!DP_IN(u, P.n_u))
+            continue;
         const CtrlRec r = s_ctrl[u];
         if (!r.ok || r.d != d)
             continue;
@@ -178,7 +190,8 @@ __device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, in
             else
                 break;
         }
-        stk[n++] = (short)u;
+        if (DP_IN(n, MAX_MEMBERS))
+            stk[n++] = (short)u;
     }
     for (int q = 0; q < n; ++q)
         s_ctrl[stk[q]].ok = 2;
@@ -201,6 +214,8 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     // standing at a light node under the literal Eq. 5c (light_model 2)
     const bool stand = P.light_model == 2 && v == 0.f && tb.light_of_node[k] >= 0;
     const size_t row = (size_t)k * P.n_v + i;
+    if (!DP_IN(row, (size_t)P.N * P.n_v))
+        return;
     ClassRec *cls_row = sc.cls + row * P.n_cls;
     ClassEntry *ent_row = sc.ent + row * P.n_cls;
     SplitRec *spl_row = sc.spl + row * P.n_u;
@@ -254,7 +269,8 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     for (int u = threadIdx.x; u < P.n_u; u += blockDim.x) {
         int ie, im, b;
         decode_u(P, u, ie, im, b);
-        const ClassRec C = cls_row[class_of(P, ie, im, b)];
+        const int cu = class_of(P, ie, im, b);
+        const ClassRec C = DP_IN(cu, P.n_cls) ? cls_row[cu] : ClassRec{};
         CtrlRec r = {0.f, 0.f, 0, 0};
         float I;
         const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
@@ -304,7 +320,8 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
             mem = class_members(P, c);
             const int b = c / (P.n_cls / P.n_b);
             for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
-                const CtrlRec r = s_ctrl[(ie * P.n_tm + member_im(mem, ie)) * P.n_b + b];
+                const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
+                const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
                 if (r.ok) {
                     ++nfeas;
                     ++nspl;
@@ -330,12 +347,13 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
                 for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
                     const int im = member_im(mem, ie);
                     const int u = (ie * P.n_tm + im) * P.n_b + b;
-                    const CtrlRec r = s_ctrl[u];
+                    const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
                     const bool in4 = r.d >= -2 && r.d <= 1;
                     if (bucket < 4 ? (r.ok != 2 || r.d != bucket - 2) : (!r.ok || in4))
                         continue;
                     const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(r.d & 0xffff) << 16);
-                    spl_row[pos] = SplitRec{r.cost, r.f, bits, 0u};
+                    if (DP_IN(pos, P.n_u))
+                        spl_row[pos] = SplitRec{r.cost, r.f, bits, 0u};
                     ++pos;
                     ++cnt;
                 }
@@ -344,7 +362,8 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
                 else
                     E.n_other = cnt;
             }
-            ent_row[ent_idx] = E;
+            if (DP_IN(ent_idx, P.n_cls))
+                ent_row[ent_idx] = E;
         }
         ent_carry += ent_tot;
         spl_carry += spl_tot;
@@ -398,6 +417,8 @@ __global__ void __launch_bounds__(256) precompute_batched_kernel(const DevParams
     __syncthreads();
     const BatchInst &I = inst[s_b];
     const long long r = blk - I.row_off;
+    if (!DP_IN(r, (long long)P.N * P.n_v))
+        return;
     precompute_row(P, I.tb, (int)(r / P.n_v), (int)(r % P.n_v), I.sc, reinterpret_cast<CtrlRec *>(pre_smem),
                    scan_buf);
 }
@@ -417,8 +438,9 @@ __global__ void terminal_batched_kernel(const DevParams *__restrict__ params, co
         const int l = s % P.n_t;
         const int j = (s / P.n_t) % P.n_xi;
         const int i = s / (P.n_t * P.n_xi);
-        VN[((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l] =
-            terminal_cost(P, node_val(P.v_lo, P.v_span, i, P.n_v), node_val(P.xi_lo, P.xi_span, j, P.n_xi));
+        const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
+        if (DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t))
+            VN[o] = terminal_cost(P, node_val(P.v_lo, P.v_span, i, P.n_v), node_val(P.xi_lo, P.xi_span, j, P.n_xi));
     }
 }
 

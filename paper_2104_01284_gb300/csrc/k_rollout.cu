@@ -14,7 +14,12 @@
 
 #include "ecodp_internal.cuh"
 
+#undef ECODP_FILE_TAG
+#define ECODP_FILE_TAG 3
+
 namespace ecodp {
+
+ECODP_CHECK_ACCESSOR(check_word_rollout)
 
 namespace {
 
@@ -51,7 +56,8 @@ __device__ float interp_cont(const DevParams &P, const float *__restrict__ Vn, f
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 float wc = c ? ft : __fsub_rn(1.f, ft);
-                float val = Vn[((size_t)(iv + a) * P.xi_rows + (ix + b + 1)) * P.ld_t + (it + c)];
+                const size_t o = ((size_t)(iv + a) * P.xi_rows + (ix + b + 1)) * P.ld_t + (it + c);
+                float val = DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t) ? Vn[o] : V_BIG;
                 acc = __fmaf_rn(__fmul_rn(__fmul_rn(wa, wb), wc), val, acc);
             }
         }
@@ -74,8 +80,12 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
     const float p = tb.grade[k];
     const float sq = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(p, p)));
     const float F_road = road_load(P, v, __fdiv_rn(p, sq), __fdiv_rn(1.f, sq));
-    const int nl = tb.light_of_node[k + 1];
-    const int lk = tb.light_of_node[k];
+    int nl = tb.light_of_node[k + 1];
+    int lk = tb.light_of_node[k];
+    if (!DP_IN(nl + 1, P.n_lights + 1))
+        nl = -1;
+    if (!DP_IN(lk + 1, P.n_lights + 1))
+        lk = -1;
     const float one_m_gamma = __fsub_rn(1.f, P.gamma);
     if (P.light_model == 2 && lk >= 0 && v == 0.f) {
         // literal Eq. 5c at the line: the zero-speed step (engine off) jumps to
@@ -303,6 +313,8 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
                 cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
 #pragma unroll
                 for (int r = 0; r < CS; ++r) {
+                    if (!DP_IN(r, (int)cl.num_blocks()))
+                        break;
                     const Cand c = *cl.map_shared_rank(mine, (unsigned)r);
                     if (c.F < w.F || (c.F == w.F && c.u < w.u))
                         w = c;
@@ -318,7 +330,7 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
                 s_t += (double)s.wait + (double)s.dt;
                 s_v = s.v1;
                 s_xi = s.xi1;
-                if (rank == 0) {
+                if (rank == 0 && DP_IN(k, N)) {
                     out_u[k] = w.u;
                     o_dt[k] = s.dt;
                     o_wait[k] = s.wait;

@@ -11,7 +11,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libecodp.so")
+# ECODP_LIBRARY=checked loads the bounds-checked build (a debugging aid)
+CHECKED = os.environ.get("ECODP_LIBRARY", "") == "checked"
+LIB_PATH = os.path.join(HERE, "libecodp_checked.so" if CHECKED else "libecodp.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_2104_01284_gb300.build.build() "
@@ -105,6 +107,23 @@ class DPError(RuntimeError):
 def check(status: int, where: str):
     if status != DP_OK:
         raise DPError(status, where)
+
+# bounds-check report of the checked build (0 / no-op in the production build)
+dp_debug_checks = _sig("dp_debug_checks", C.POINTER(C.c_int32), C.POINTER(C.c_uint64))
+EXPORTED.append("dp_debug_checks")
+
+
+def debug_checks():
+    """(enabled, site): whether this is the bounds-checked build, and its first
+    recorded failure (0 if none; cleared by the read).  Synchronises the
+    device."""
+    en = C.c_int32(0)
+    site = C.c_uint64(0)
+    st = dp_debug_checks(C.byref(en), C.byref(site))
+    if st not in (DP_OK, DP_ERR_INTERNAL):
+        check(st, "dp_debug_checks")
+    return bool(en.value), int(site.value)
+
 
 # allocation-free single stage (static device working memory)
 dp_solve_stage_static = _sig("dp_solve_stage_static", C.POINTER(ProblemDesc), C.c_int32, vp, vp, vp, vp)

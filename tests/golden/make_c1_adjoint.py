@@ -1,0 +1,98 @@
+"""Write the FP64 oracle's adjoint dJ_0(x0)/dtheta for paper-scale instances.
+
+Calls only the oracle and the seeded problem generator.  For the 100-stage,
+51 x 51 x 201-state, 1922-control instance family (seed 1, then seeds from
+100 upward) it runs the nominal backward sweep and the oracle's forward
+lambda sweep at x0 = (10 m/s, 0.55, 0 s) and stores, per seed s:
+
+  grad_s<s>   dJ_0(x0)/dtheta, theta = (mass, CdA, Crr, R0, fuel scale)
+  J0_s<s>     J_0(x0)
+  diag_s<s>   [status, support size, snapped, infeasible corner, min gap,
+               snapped lambda mass]
+  tie_s<s>    lambda mass on support states whose best-vs-second gap is at
+              most TIE_GAPS[i] (relative), i = 0..3
+  top_s<s>    the TOP support states with the largest lambda: flat index over
+              the states of stages 0..N-1 (stage k at k * n_states), lambda,
+              nominal argmin and relative gap, as columns of a float64 array
+
+The lambda mass of all stages is N = 100 (one per stage).  A seed is
+"stable" for a comparison of an FP32 solver's adjoint with this one when x0
+is feasible, no infeasible corner enters a value or gradient on the support,
+no lambda mass sits on a snapped fraction and at most STABLE_MASS of lambda
+mass sits on states whose gap is at most 1e-5 (ten times an FP32 solver's
+accumulated relative value error, so such a solver takes every other
+decision on the support as the oracle does).  Finite differences of a
+paper-scale sweep would need ten further sweeps per seed (about 40
+CPU-minutes each), so they are checked on smaller instances
+(make_adjoint_fd.py).  The scan stops once three seeds from 100 upward are
+stable, or after seven of them; results are saved after every seed.
+
+Usage: python tests/golden/make_c1_adjoint.py [nthreads]
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from paper_2104_01284_gb300 import problems as P  # noqa: E402
+
+PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c1_adjoint.npz")
+TIE_GAPS = (1e-4, 1e-5, 1e-6, 1e-7)
+STABLE_MASS = 1e-2
+TOP = 3000
+
+
+def stable(out, seed) -> bool:
+    status, _, _, corner, _, snap_mass = out[f"diag_s{seed}"]
+    return status == 0 and corner == 0 and snap_mass == 0 and out[f"tie_s{seed}"][1] <= STABLE_MASS
+
+
+def main(nthreads: int = 0):
+    out = dict(np.load(PATH)) if os.path.exists(PATH) else {}
+    out["tie_gaps"] = np.array(TIE_GAPS)
+    seeds = [1] + list(range(100, 107))
+    n_stable = sum(stable(out, s) for s in seeds if s >= 100 and f"diag_s{s}" in out)
+    for seed in seeds:
+        if f"diag_s{seed}" in out:
+            continue
+        if seed >= 100 and n_stable >= 3:
+            break
+        p = P.config1(seed=seed)
+        op = O.make(p)
+        t0 = time.time()
+        Vs, _, _ = O.solve(op, O.NOMINAL, nthreads=nthreads)
+        g, d, _, rc = O.adjoint(op, p.x0, want_lam=True)
+        J0 = O.interp(op, 0, Vs[0], *p.x0)
+        n = p.n_states * p.n_stages  # states of stages 0..N-1 (uniform grids)
+        lam = d["lam"][:n]
+        best = op._Vall[:n]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            gap = (op._secall[:n] - best) / np.abs(best)
+        on = lam > 0
+        out[f"grad_s{seed}"] = g
+        out[f"J0_s{seed}"] = np.float64(J0)
+        out[f"diag_s{seed}"] = np.array([rc, d["support_size"], d["snapped"], d["infeasible_corner"], d["min_gap"],
+                                         d["snapped_mass"]], np.float64)
+        out[f"tie_s{seed}"] = np.array([float(lam[on & ~(gap > q)].sum()) for q in TIE_GAPS])
+        top = np.argsort(-lam)[:TOP]
+        top = top[lam[top] > 0]
+        out[f"top_s{seed}"] = np.stack([top.astype(np.float64), lam[top], op._piall[:n][top].astype(np.float64),
+                                        gap[top]], axis=1)
+        if seed >= 100 and stable(out, seed):
+            n_stable += 1
+        print(f"seed {seed}: {time.time() - t0:.0f} s, J0 {J0:.6f}, grad {g}, diag {out[f'diag_s{seed}']}, "
+              f"tie masses {out[f'tie_s{seed}']}, stable {stable(out, seed)}", flush=True)
+        del Vs
+        op._Vall = op._piall = op._secall = None
+        np.savez_compressed(PATH + ".tmp.npz", **out)
+        os.replace(PATH + ".tmp.npz", PATH)
+    print("wrote", PATH, flush=True)
+
+
+if __name__ == "__main__":
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 0)

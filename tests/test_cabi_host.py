@@ -36,6 +36,21 @@ def test_exports_every_declared_function(native):
     assert set(native.EXPORTED) == set(names)
 
 
+def test_checked_build_exports_the_same_functions(native):
+    """The bounds-checked variant (ECODP_CHECKS) exports the same C ABI and
+    reports itself as checked; the production build reports unchecked.
+    Neither query touches the device."""
+    from paper_2104_01284_gb300 import build
+    path = build.build(checks=True)
+    chk = C.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(chk, n), n
+    for lib_, want in ((native.lib, 0), (chk, 1)):
+        en = C.c_int32(-1)
+        assert lib_.dp_debug_checks(C.byref(en), None) == 0
+        assert en.value == want
+
+
 def test_status_strings(native):
     assert native.lib.dp_status_string(0) == b"DP_OK"
     assert native.lib.dp_status_string(4) == b"DP_ERR_INFEASIBLE"
