@@ -39,9 +39,10 @@
 // Argmin order: (value, torque class, control index).  Among controls with
 // exactly equal FP32 values the first class in class order (brake flag
 // slowest, then total torque ascending) wins, then the lowest control index
-// inside it.  Exact FP32 ties are rounding coincidences of near-equal costs (the
-// FP64 recursion has none on the seeded instances); resolving them toward the
-// lowest global control index would re-evaluate every tied class.
+// inside it.  An exact FP32 tie between classes means FP64 values closer than
+// the FP32 rounding (on the paper-scale sweep 1.5 % of the feasible states
+// have one); resolving it toward the lowest global control index would
+// re-evaluate every class of such a state in the argmin recovery.
 #pragma once
 
 #include <climits>
