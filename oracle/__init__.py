@@ -95,7 +95,7 @@ def lib():
             L.orc_rollout.argtypes = [P, vp, vp, vp, vp, vp, vp]
             L.orc_sequence_cost.argtypes = [P, vp, vp, vp]
             L.orc_sequence_cost.restype = C.c_double
-            L.orc_adjoint.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_adjoint.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, vp]
             L.orc_eval.argtypes = [P, C.c_int, C.c_int, vp, C.c_double, C.c_double, C.c_double,
                                    C.c_int, C.c_int, C.c_int, vp]
             L.orc_eval.restype = C.c_double
@@ -276,20 +276,25 @@ def rollout(op: OracleProblem, Vs, x0=None):
 THETA = ("mass", "cda", "crr", "r0", "fuel_scale")
 
 
-def adjoint(op: OracleProblem, x0=None):
+def adjoint(op: OracleProblem, x0=None, want_lam: bool = False):
     """dJ_0(x0)/dtheta for theta = THETA by the forward lambda sweep, on the
     nominal solution of the last `solve(op)` call.  Returns (grad[5], diag
-    dict, support flags over the states of stages 0..N-1, status)."""
+    dict, support flags over the states of stages 0..N-1, status); with
+    want_lam the diag dict also holds "lam", the lambda of every state (same
+    layout as the support flags)."""
     if getattr(op, "_piall", None) is None:
         raise RuntimeError("call solve(op) first")
     x0 = np.array(op.p.x0 if x0 is None else x0, np.float64)
     grad = np.zeros(5)
     diag = np.zeros(6)
     support = np.zeros(op._Vall.size, np.uint8)
+    lam = np.zeros(op._Vall.size, np.float64) if want_lam else None
     rc = lib().orc_adjoint(op.ref, _ptr(op._Vall), _ptr(op._piall), _ptr(op._secall), _ptr(x0), _ptr(grad),
-                           _ptr(diag), _ptr(support))
+                           _ptr(diag), _ptr(support), _ptr(lam) if want_lam else None)
     d = dict(support_size=int(diag[0]), snapped=bool(diag[1]), infeasible_corner=bool(diag[2]),
              min_gap=float(diag[3]), near_tie_mass=float(diag[4]), snapped_mass=float(diag[5]))
+    if want_lam:
+        d["lam"] = lam
     return grad, d, support, int(rc)
 
 

@@ -826,10 +826,11 @@ static int interp_grad(const orc_problem *P, int stage, const double *V, double 
  * NaN), and the lambda mass on support states whose successor met a snapped
  * fraction.  The two masses bound how much of the gradient rests on
  * decisions that a lower-precision solver may take differently.  support (optional, [total states of stages 0..N-1]) receives the
- * support as 0/1 flags.  Returns ORC_ERR_INFEASIBLE if the support reaches an
- * infeasible state. */
+ * support as 0/1 flags, lam_out (optional, same size) the lambda of every
+ * state (0 off the support).  Returns ORC_ERR_INFEASIBLE if the support
+ * reaches an infeasible state. */
 int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, const double *secall,
-                const double *x0, double *grad, double *diag, uint8_t *support)
+                const double *x0, double *grad, double *diag, uint8_t *support, double *lam_out)
 {
     int N = P->n_stages;
     double *lam = calloc((size_t)P->V_off[N + 1], sizeof(double));
@@ -873,6 +874,8 @@ int orc_adjoint(const orc_problem *P, const double *Vall, const int32_t *piall, 
             diag[0] += 1;
             if (support)
                 support[base + s] = 1;
+            if (lam_out)
+                lam_out[base + s] = L;
             int u = piall[base + s];
             if (u < 0) {
                 status = ORC_ERR_INFEASIBLE;
