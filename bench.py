@@ -39,7 +39,7 @@ FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample e
 # of this workload) from an ncu capture of the current kernel version (ncu's
 # counters cannot be read inside a timed run).  None whenever the kernel has
 # changed since the last capture.
-BELLMAN_TRAFFIC_BYTES = 3.732992e6
+BELLMAN_TRAFFIC_BYTES = 3.734016e6
 
 
 def parse():
