@@ -176,8 +176,8 @@ def test_paper_scale_adjoint_matches_the_oracle(gpu):
     mod = _load_script("make_c1_adjoint")
     g = dict(np.load(path))
     seeds = sorted(int(k[6:]) for k in g if k.startswith("diag_s"))
-    stable = [s for s in seeds if s >= 100 and mod.stable(g, s)]
-    assert 1 in seeds and len(stable) >= 3, (seeds, stable)
+    stable = [s for s in seeds if mod.stable(g, s)]
+    assert 1 in seeds and sum(s >= 100 for s in stable) >= 3, (seeds, stable)
     for seed in seeds:
         if g[f"diag_s{seed}"][0] != 0:
             continue  # x0 infeasible in the oracle
