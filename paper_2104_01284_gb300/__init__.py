@@ -7,9 +7,12 @@ a C ABI (include/ecodp.h, libecodp.so).
 
 Modules:
   problems  seeded synthetic problem instances (no solver arithmetic)
-  native    ctypes binding of libecodp.so (fails loudly if it is not built)
-  solver    EcoDP: PyTorch-facing wrapper (device memory, streams)
-  build     nvcc build of libecodp.so
+  native    ctypes binding of libecodp.so (fails loudly if it is not built;
+            ECODP_LIBRARY=checked loads the bounds-checked build instead)
+  solver    EcoDP, EcoDPBatch, EcoDPValue: PyTorch-facing wrappers (device
+            memory, streams, autograd of the adjoint)
+  serving   EcoDPServer and the simulated fleet for receding-horizon re-solves
+  build     nvcc build of libecodp.so and libecodp_checked.so
 """
 
 __all__ = ["EcoDP", "problems"]
