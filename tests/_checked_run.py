@@ -54,6 +54,24 @@ def main():
     dp.adjoint((10.0, 0.55, 0.0))
     clean("adjoint", done)
     dp.close()
+    # the allocation-free stage on the reduced problem
+    import ctypes as C
+    from paper_2104_01284_gb300.solver import make_desc
+    p = probs["reduced"]
+    desc, keep = make_desc(p)
+    vn = torch.from_numpy(P.synthetic_value_field(p, seed=6).astype(np.float32)).cuda()
+    v_out = torch.empty_like(vn)
+    pi_out = torch.empty(vn.shape, dtype=torch.int16, device="cuda")
+    N.check(N.dp_solve_stage_static(C.byref(desc), int(p.light_stage[0]), vn.data_ptr(), v_out.data_ptr(),
+                                    pi_out.data_ptr(), torch.cuda.current_stream().cuda_stream),
+            "dp_solve_stage_static")
+    clean("static_stage", done)
+    # three fleet-shaped requests through the serving loop
+    from paper_2104_01284_gb300.serving import EcoDPServer
+    from tests.test_gpu_serving import fleet_requests_with_lights, serve_all
+    with EcoDPServer(max_slots=2) as srv:
+        serve_all(srv, fleet_requests_with_lights(3))
+    clean("serving", done)
     # a 4-instance uneven batch in one persistent launch, and its rollouts
     with EcoDPBatch(P.config3_small(seed=34, n_instances=4)) as bt:
         bt.solve()
