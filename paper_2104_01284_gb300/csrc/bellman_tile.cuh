@@ -39,10 +39,13 @@
 // Argmin order: (value, torque class, control index).  Among controls with
 // exactly equal FP32 values the first class in class order (brake flag
 // slowest, then total torque ascending) wins, then the lowest control index
-// inside it.  An exact FP32 tie between classes means FP64 values closer than
-// the FP32 rounding (on the paper-scale sweep 1.5 % of the feasible states
-// have one); resolving it toward the lowest global control index would
-// re-evaluate every class of such a state in the argmin recovery.
+// inside it.  Exact ties between classes are structural (classes with the
+// same successor window reaching the value with lines of equal cost, such as
+// a stop at the line with and without the brake flag); on the paper-scale
+// sweep 1.5 % of the feasible states have one, and for 99 % of those the
+// first class also holds the lowest control index.  Resolving the rest
+// toward the lowest global index would re-evaluate every later class of such
+// a state in the argmin recovery.
 #pragma once
 
 #include <climits>
