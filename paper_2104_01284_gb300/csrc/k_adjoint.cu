@@ -220,10 +220,16 @@ __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const floa
         out[6] = 1.0;  // x0 off the grid
         return;
     }
+    // only the corners with non-zero weight enter J_0(x0) and lam_0 (x0 does
+    // not depend on theta, so the slopes of the interpolant there are unused):
+    // an infeasible neighbour that only the slopes would read is no failure
     double J = 0.0;
+    bool value_bad = false;
     for (int q = 0; q < 8; ++q) {
         if (r.w[q] == 0.f)
             continue;
+        if (!(V0[r.corner[q]] < V_FEAS_MAX))
+            value_bad = true;
         const size_t s = (r.corner[q] / P.ld_t / P.xi_rows) * (size_t)P.n_xi * P.n_t +
                          ((r.corner[q] / P.ld_t) % P.xi_rows - 1) * (size_t)P.n_t + r.corner[q] % P.ld_t;
         if (!DP_IN(s, n))
@@ -232,8 +238,8 @@ __global__ void adjoint_init_kernel(const DevParams *__restrict__ dP, const floa
         frontier_add(F, 0, 0, n, (int)s);
         J += (double)r.w[q] * (double)V0[r.corner[q]];
     }
-    out[5] = r.bad ? __longlong_as_double(0x7ff0000000000000LL) : J;
-    if (r.bad)
+    out[5] = value_bad ? __longlong_as_double(0x7ff0000000000000LL) : J;
+    if (value_bad)
         out[6] = 2.0;
 }
 
