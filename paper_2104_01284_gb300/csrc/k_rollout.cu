@@ -135,7 +135,13 @@ __device__ bool model_step(const DevParams &P, const StageTables &tb, int k, flo
     return true;
 }
 
-constexpr int ROLL_THREADS = 1024;
+// Threads of a rollout CTA: the cluster's 8 CTAs share one stage's controls
+// (~240 each at the paper-scale size), so 256 threads give every thread one
+// control with the cheapest block reduction (1024 threads: 0.59 vs 0.47 ms
+// per paper-scale rollout); a batched rollout's single CTA per instance takes
+// every control itself and keeps 1024.
+constexpr int ROLL_THREADS = 256;
+constexpr int ROLL_THREADS_BATCHED = 1024;
 constexpr int ROLL_CLUSTER = 8;  // CTAs (SMs) of the single-problem rollout
 
 // A CTA's best control of a stage.
@@ -164,8 +170,8 @@ __device__ void rollout_body(const DevParams *__restrict__ dP, const StageTables
     __shared__ DevParams P;
     __shared__ float s_v, s_xi;
     __shared__ double s_t, s_fuel, s_J;
-    __shared__ float red_F[ROLL_THREADS / 32];
-    __shared__ int red_u[ROLL_THREADS / 32];
+    __shared__ float red_F[ROLL_THREADS_BATCHED / 32];
+    __shared__ int red_u[ROLL_THREADS_BATCHED / 32];
     __shared__ int s_fail;
     // this CTA's candidate, double-buffered by stage parity: the cluster's
     // CTAs read it after the stage's cluster barrier, and a CTA can only
@@ -369,7 +375,7 @@ __global__ void __cluster_dims__(ROLL_CLUSTER, 1, 1) __launch_bounds__(ROLL_THRE
 
 // Batched: one CTA per instance; instance b writes its output block at
 // out + out_off[b] (doubles) and out_u + u_off[b].
-__global__ void __launch_bounds__(ROLL_THREADS)
+__global__ void __launch_bounds__(ROLL_THREADS_BATCHED)
     rollout_batched_kernel(const DevParams *__restrict__ params, const BatchInst *__restrict__ inst,
                            const double *__restrict__ x0, const long long *__restrict__ out_off,
                            const long long *__restrict__ u_off, double *__restrict__ out, int *__restrict__ out_u)
@@ -399,7 +405,7 @@ cudaError_t launch_rollout_batched(const DevParams *params, const BatchInst *ins
                                    const long long *out_off, const long long *u_off, double *out, int *out_u,
                                    cudaStream_t s)
 {
-    rollout_batched_kernel<<<n_inst, ROLL_THREADS, 0, s>>>(params, inst, x0, out_off, u_off, out, out_u);
+    rollout_batched_kernel<<<n_inst, ROLL_THREADS_BATCHED, 0, s>>>(params, inst, x0, out_off, u_off, out, out_u);
     return cudaGetLastError();
 }
 
