@@ -168,8 +168,10 @@ def test_paper_scale_adjoint_matches_the_oracle(gpu):
     need ten more 100-stage sweeps per seed).  On every stored seed the GPU
     value J_0(x0) matches and the GPU policy equals the oracle's at the
     largest-lambda support states wherever the oracle's gap exceeds 1e-4
-    (acceptance (c) on the support); on the stable seeds (little lambda mass
-    on near-ties) the GPU adjoint is within 1e-3 relative of the oracle's."""
+    (acceptance (c) on the support); on the stable seeds (feasible start,
+    at most 1e-3 of the lambda mass on snapped interpolation fractions) the
+    GPU adjoint is within 1e-3 relative of the oracle's, near-ties on the
+    support included."""
     path = os.path.join(GOLDEN, "c1_adjoint.npz")
     if not os.path.exists(path):
         pytest.skip("golden file not generated")
