@@ -61,6 +61,10 @@ struct dp_problem {
     int *d_rowcnt = nullptr;
     SplitRec *d_spl = nullptr;
     float *d_pad_in = nullptr, *d_pad_out = nullptr, *d_dense = nullptr;
+    // corner quads of J_k for the tiled sweep, two slots by stage parity
+    // (launch_quad_from_pad); padding entries hold V_BIG for the object's life
+    float4 *d_quad = nullptr;
+    float4 *quad(int k) const { return d_quad + (size_t)(k & 1) * stage_elems; }
     int16_t *d_pi_tmp = nullptr;
     double *d_roll = nullptr;
     int *d_roll_u = nullptr;
@@ -433,17 +437,26 @@ dp_status upload_tables(dp_problem *p, cudaStream_t s)
     return DP_OK;
 }
 
-// The backward sweep's launches: terminal values, the precompute tables of
-// every stage (they depend on the route, not on J), then the N Bellman
-// stages in backward order.
+// Stage k of a full backward sweep: J_{k+1} and its corner quads in, J_k,
+// pi_k and J_k's quads out (the tiled kernel keeps the quads of every stage;
+// the other paths ignore them).
+cudaError_t sweep_stage(dp_problem *p, int k, cudaStream_t s)
+{
+    return launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
+                          p->variant, s, p->quad(k + 1), p->quad(k));
+}
+
+// The backward sweep's launches: terminal values (and their corner quads),
+// the precompute tables of every stage (they depend on the route, not on J),
+// then the N Bellman stages in backward order.
 dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 {
     DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
     DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(p->N), s));
+    DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(p->N), p->quad(p->N), s));
     DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, p->N, p->scratch(), s));
     for (int k = p->N - 1; k >= 0; --k)
-        DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
-                               p->variant, s));
+        DP_CUDA(sweep_stage(p, k, s));
     return DP_OK;
 }
 
@@ -591,6 +604,7 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, rows * P.n_cls, &p->d_ent));
     TRY(dev_alloc_n(p, rows * 2, &p->d_rowcnt));
     TRY(dev_alloc_n(p, rows * P.n_u, &p->d_spl));
+    TRY(dev_alloc_n(p, 2 * p->stage_elems, &p->d_quad));
     TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_in));
     TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_out));
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_dense));
@@ -613,6 +627,8 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(cuda_try(cudaMemsetAsync(p->d_part, 0xff, p->pi_elems * sizeof(unsigned long long), p->create_stream),
                  "clear split minima"));
     // every padding cell holds the infeasible sentinel for the object's life
+    TRY(cuda_try(launch_fill(reinterpret_cast<float *>(p->d_quad), 8 * p->stage_elems, V_BIG, p->create_stream),
+                 "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
@@ -781,13 +797,13 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
         DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
         DP_CUDA(cudaEventRecord(ev[0], s));
         DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(N), s));
+        DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(N), p->quad(N), s));
         DP_CUDA(cudaEventRecord(ev[1], s));
         DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, N, p->scratch(), s));
         DP_CUDA(cudaEventRecord(ev[2], s));
         for (int k = N - 1, q = 3; k >= 0; --k, ++q) {
             NvtxRange stage_range(("ecodp.stage " + std::to_string(k)).c_str());
-            DP_CUDA(launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
-                                   p->variant, s));
+            DP_CUDA(sweep_stage(p, k, s));
             DP_CUDA(cudaEventRecord(ev[q], s));
         }
         DP_CUDA(cudaEventSynchronize(ev[N + 2]));

@@ -29,7 +29,10 @@
 // of any other shift sit behind one warp-uniform test per class.  Two rows go
 // through one packed FP32 FMA (__ffma2_rn) and two lines through one
 // three-input min.  Two consecutive classes with the same speed cell and time
-// shift share the loads of their window.  Only class minima are tracked in
+// shift share the loads of their window.  In a single-problem sweep (QUAD)
+// the inner window rows come from corner quads of J_{k+1}, one 16-byte load
+// per row instead of four, and the epilogue writes J_k's quads for the next
+// stage.  Only class minima are tracked in
 // the sweep; afterwards each warp buckets its states by winning class in
 // shared memory and re-evaluates that class (bit for bit the same arithmetic)
 // to recover the argmin.  An arrival during red points the class's time
@@ -373,6 +376,44 @@ __device__ __forceinline__ int class_lowest_u_global(const DevParams &P, const T
     return ub;
 }
 
+// One corner quad of J_{k+1} (launch_quad_from_pad): the cell's two time
+// columns at speed rows iv and iv + 1, read-only with the L1 evict-last hint.
+__device__ __forceinline__ float4 ldq(const float4 *p)
+{
+    float4 v;
+    asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// class_window and pair_window on the corner quads (q0: the quad of the
+// window's lower corner at padded SoC row 0): one load per window row, the
+// same blend.
+template <int R>
+__device__ __forceinline__ void class_window_q(const float4 *q0, const TCtx &x, const int (&roff)[R + 4],
+                                               float (&G)[R + 4])
+{
+#pragma unroll
+    for (int w = 1; w < R + 3; ++w) {
+        const float4 c = ldq(q0 + roff[w]);
+        G[w] = blend_raw(make_float2(c.x, c.y), make_float2(c.z, c.w), x.wv0, x.wv1, x.wt0, x.wt1);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void pair_window_q(const float4 *q0, const TCtx &x, const int (&roff)[R + 4], float bv0,
+                                              float bv1, float bt0, float bt1, float (&G)[R + 4], float (&H)[R + 4])
+{
+#pragma unroll
+    for (int w = 1; w < R + 3; ++w) {
+        const float4 c = ldq(q0 + roff[w]);
+        const float2 lo = make_float2(c.x, c.y), hi = make_float2(c.z, c.w);
+        G[w] = blend_raw(lo, hi, x.wv0, x.wv1, x.wt0, x.wt1);
+        H[w] = blend_raw(lo, hi, bv0, bv1, bt0, bt1);
+    }
+}
+
 // Inner window of one class: blended values at SoC rows jb - 1 .. jb + R
 // (G[1 .. R + 2]; row offsets roff), which the buckets d = -1 and d = 0 read.
 template <int R, bool NC>
@@ -526,12 +567,13 @@ __device__ __forceinline__ unsigned long long pack_min(float v, int e)
     return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)e;
 }
 
-template <int R, bool NC, int MODE = TILE_FULL>
+template <int R, bool NC, int MODE = TILE_FULL, bool QUAD = false>
 __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, const ClassRec *g_cls,
                              const ClassEntry *g_ent, const SplitRec *g_spl, int n_ent, int n_spl, const float *Vn,
                              float *__restrict__ Vk, int16_t *__restrict__ pik, int i, int chunk,
                              unsigned char *smem_raw, unsigned long long *stats, int e_begin = 0, int e_end = 0,
-                             unsigned long long *__restrict__ part = nullptr)
+                             unsigned long long *__restrict__ part = nullptr, const float4 *__restrict__ Qn = nullptr,
+                             float4 *__restrict__ Qk = nullptr)
 {
     const int tid = threadIdx.x;
     const Layout L = layout<R>(P.n_cls, P.n_u);
@@ -635,10 +677,18 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 T2 = s_tc[e + 1];
                 have_h = T2.ivst == T.ivst;
             }
-            if (have_h)
+            if (QUAD) {
+                // the quad at the same flat index as the window's lower corner
+                const float4 *q0 = Qn + (x.p0 - Vn);
+                if (have_h)
+                    pair_window_q<R>(q0, x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft, G, H);
+                else
+                    class_window_q<R>(q0, x, roff, G);
+            } else if (have_h) {
                 pair_window<R, NC>(x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft, G, H);
-            else
+            } else {
                 class_window<R, NC>(x, roff, G);
+            }
         }
         // SoC differences Dg[w] = G[w + 1] - G[w] as even-aligned pairs EV[p]
         // = {Dg[2p], Dg[2p + 1]} and odd-aligned pairs OD[p] = {Dg[2p + 1],
@@ -731,9 +781,22 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const size_t ov = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
         const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + l;
         if (valid && DP_IN(ov, (size_t)P.n_v * P.xi_rows * P.ld_t) && DP_IN(op, (size_t)P.n_v * P.n_xi * P.n_t)) {
-            Vk[ov] = feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
+            const float val = feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
+            Vk[ov] = val;
             if (!feas)
                 pik[op] = -1;
+            if (QUAD) {
+                // J_k's value in the four quads that hold it (ov >= ld_t: the
+                // state sits below padding row -1; speed row i - 1 from i > 0)
+                float *qf = reinterpret_cast<float *>(Qk);
+                const size_t vrow = (size_t)P.xi_rows * P.ld_t;
+                qf[4 * ov] = val;
+                qf[4 * (ov - 1) + 1] = val;
+                if (i > 0) {
+                    qf[4 * (ov - vrow) + 2] = val;
+                    qf[4 * (ov - vrow - 1) + 3] = val;
+                }
+            }
         }
     }
     if (stats) {

@@ -337,8 +337,19 @@ cudaError_t launch_terminal(const DevParams *dP, const DevParams &hP, float *VN,
 // Tables of stages k_first .. k_first + n_k - 1 (one CTA per speed row and stage).
 cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k_first, int n_k,
                               StageScratch sc, cudaStream_t s);
+// Corner quads of a padded value array: Q[q] = {V[q], V[q + 1], V[q + vrow],
+// V[q + vrow + 1]} for every flat index q of the padded layout (vrow =
+// xi_rows ld_t, one speed row; entries past the array read V_BIG), i.e. the
+// two time columns of a cell at speed rows iv and iv + 1.  A Bellman tile
+// reads a window row of J_{k+1} with one 16-byte load instead of four.
+cudaError_t launch_quad_from_pad(const DevParams &hP, const float *V, float4 *Q, cudaStream_t s);
+// One Bellman stage.  With Qn and Qk (corner quads of J_{k+1} and J_k, the
+// latter written by the launch) the tiled kernel reads its windows from Qn;
+// every other path ignores them, so a sweep must pass them at every stage or
+// at none.
 cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
-                           const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s);
+                           const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s,
+                           const float4 *Qn = nullptr, float4 *Qk = nullptr);
 cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float *padded, cudaStream_t s);
 cudaError_t launch_dense_from_pad(const DevParams &hP, const float *padded, float *dense, cudaStream_t s);
 // Where J_k lives for the stages a launch reads: base + (k - k_base)

@@ -84,10 +84,13 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     }
 }
 
-template <int R>
+// QUAD: windows read from the corner quads Qn of J_{k+1}, J_k's quads written
+// to Qk (a sweep whose every stage takes this kernel).
+template <int R, bool QUAD>
 __global__ void __launch_bounds__(TLANES, tile_minb<R>())
     bellman_tiled(const DevParams *__restrict__ dP, StageTables tb, int k, StageScratch sc,
-                  const float *__restrict__ Vn, float *__restrict__ Vk, int16_t *__restrict__ pik)
+                  const float *__restrict__ Vn, float *__restrict__ Vk, int16_t *__restrict__ pik,
+                  const float4 *__restrict__ Qn, float4 *__restrict__ Qk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevParams P;
@@ -99,9 +102,9 @@ __global__ void __launch_bounds__(TLANES, tile_minb<R>())
     // come last and fill the SMs that received a fourth CTA
     const int i = gridDim.y - 1 - blockIdx.y;
     const size_t row = (size_t)k * P.n_v + i;
-    bellman_tile<R, true>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls, sc.spl + row * P.n_u,
-                          sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn, Vk, pik, i, blockIdx.x, smem_raw,
-                          sc.stats);
+    bellman_tile<R, true, TILE_FULL, QUAD>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
+                                           sc.spl + row * P.n_u, sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn,
+                                           Vk, pik, i, blockIdx.x, smem_raw, sc.stats, 0, 0, nullptr, Qn, Qk);
 }
 
 // Class-split tiles for grids whose tiles cannot fill the GPU: blockIdx.z
@@ -209,7 +212,7 @@ int tile_rows(const DevParams &hP)
 
 template <int R>
 cudaError_t launch_tiles(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
-                         const float *Vnext, float *Vk, int16_t *pik, cudaStream_t s)
+                         const float *Vnext, float *Vk, int16_t *pik, cudaStream_t s, const float4 *Qn, float4 *Qk)
 {
     const size_t smem = layout<R>(hP.n_cls, hP.n_u).total;
     const int chunks = chunks_per_row<R>(hP.n_xi, hP.n_t);
@@ -226,10 +229,20 @@ cudaError_t launch_tiles(const DevParams *dP, const DevParams &hP, StageTables t
         bellman_join<<<dim3((hP.n_xi * hP.n_t + 255) / 256, hP.n_v), 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
         return cudaGetLastError();
     }
-    cudaError_t err = cudaFuncSetAttribute(bellman_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (Qn && Qk) {
+        cudaError_t err =
+            cudaFuncSetAttribute(bellman_tiled<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+        bellman_tiled<R, true><<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
+        return cudaGetLastError();
+    }
+    cudaError_t err =
+        cudaFuncSetAttribute(bellman_tiled<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess)
         return err;
-    bellman_tiled<R><<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
+    bellman_tiled<R, false><<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, nullptr,
+                                                                        nullptr);
     return cudaGetLastError();
 }
 
@@ -242,7 +255,8 @@ size_t bellman_smem_bytes(const DevParams &hP)
 }
 
 cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
-                           const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s)
+                           const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s,
+                           const float4 *Qn, float4 *Qk)
 {
     if (variant == 0) {
         dim3 grid((hP.n_xi * hP.n_t + 255) / 256, hP.n_v);
@@ -250,8 +264,8 @@ cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables
         return cudaGetLastError();
     }
     const int R = variant == 2 ? 8 : (variant == 3 ? 6 : tile_rows(hP));
-    return R == 6 ? launch_tiles<6>(dP, hP, tb, k, sc, Vnext, Vk, pik, s)
-                  : launch_tiles<8>(dP, hP, tb, k, sc, Vnext, Vk, pik, s);
+    return R == 6 ? launch_tiles<6>(dP, hP, tb, k, sc, Vnext, Vk, pik, s, Qn, Qk)
+                  : launch_tiles<8>(dP, hP, tb, k, sc, Vnext, Vk, pik, s, Qn, Qk);
 }
 
 }  // namespace ecodp

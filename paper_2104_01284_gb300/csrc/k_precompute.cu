@@ -14,6 +14,8 @@
 //     (Eq. 5b), grouped inside each class by d.
 // The per-control arithmetic runs one thread per control; the grouping then
 // only reads those results back from shared memory.
+#include <algorithm>
+
 #include "ecodp_internal.cuh"
 
 #undef ECODP_FILE_TAG
@@ -71,6 +73,21 @@ __global__ void dense_from_pad_kernel(const DevParams P, const float *__restrict
         const size_t o = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
         float x = DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t) ? padded[o] : V_BIG;
         dense[s] = (x < V_FEAS_MAX) ? x : __int_as_float(0x7f800000);
+    }
+}
+
+// Corner quads of a padded value array (launch_quad_from_pad).
+__global__ void quad_from_pad_kernel(const DevParams P, const float *__restrict__ V, float4 *__restrict__ Q)
+{
+    const size_t vrow = (size_t)P.xi_rows * P.ld_t;
+    const size_t total = (size_t)P.n_v * vrow;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        float4 r;
+        r.x = V[q];
+        r.y = q + 1 < total ? V[q + 1] : V_BIG;
+        r.z = q + vrow < total ? V[q + vrow] : V_BIG;
+        r.w = q + vrow + 1 < total ? V[q + vrow + 1] : V_BIG;
+        Q[q] = r;
     }
 }
 
@@ -498,6 +515,14 @@ cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float
 {
     int total = hP.n_v * hP.n_xi * hP.n_t;
     pad_from_dense_kernel<<<(total + 255) / 256, 256, 0, s>>>(hP, dense, padded);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quad_from_pad(const DevParams &hP, const float *V, float4 *Q, cudaStream_t s)
+{
+    const size_t total = (size_t)hP.n_v * hP.xi_rows * hP.ld_t;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    quad_from_pad_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(hP, V, Q);
     return cudaGetLastError();
 }
 

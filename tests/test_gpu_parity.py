@@ -106,6 +106,36 @@ def test_tiled_and_direct_bit_identical(gpu, name):
         a.close()
 
 
+@pytest.mark.parametrize("variant", ["tiled", "tiled6"])
+def test_unsplit_tiled_sweep_bit_identical(gpu, variant):
+    """A grid with enough tiles for the unsplit tiled kernel (more than half
+    of the GPU's resident CTA slots, 4 per SM), whose sweep reads J_{k+1}
+    through the corner quads the previous stage wrote: every J_k and pi_k of
+    the sweep equals, bit for bit, the stage hook (plain loads of J_{k+1}) run
+    on the sweep's own J_{k+1}, and the direct kernel's sweep.  Two lights
+    cover the unpaired window loads of light stages."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n_soc, n_t, R = 51, 201, (8 if variant == "tiled" else 6)
+    chunks = (-(-n_soc // R) * n_t + 127) // 128
+    n_v = max(31, 2 * sms // chunks + 1)
+    assert n_v * chunks > 2 * sms  # the class-split launch is not taken
+    # 60 s for 60 m: time to wait at both lights (about half of J_0 feasible)
+    p = P.config1(seed=77, n_stages=6, n_v=n_v, n_soc=n_soc, n_t=n_t, n_te=11, n_tm=11, n_lights=2, t_hi=60.0)
+    a = gpu(p)
+    a.set_variant(variant)
+    a.solve()
+    b = gpu(p)
+    b.set_variant("direct")
+    b.solve()
+    for k in range(p.n_stages - 1, -1, -1):
+        vk, pk = a.solve_stage(k, a.value(k + 1))
+        assert torch.equal(a.value(k), vk), k
+        assert torch.equal(a.policy(k), pk), k
+        assert torch.equal(a.value(k), b.value(k)), k
+        assert torch.equal(a.policy(k), b.policy(k)), k
+    assert torch.isfinite(a.value(0)).float().mean() > 0.3
+
+
 def feasible_start(p, V0, V0lo, V0hi):
     """p.x0 if it is a robustly feasible grid node, else the node nearest to
     it (speed, then SoC, then earliest time) whose J_0 is finite in all three
