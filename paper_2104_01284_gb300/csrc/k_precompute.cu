@@ -328,25 +328,40 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     // 4. compact the feasible classes: the envelope lines of each bucket, then
     // every control of any other shift (rare: one SoC step is far larger than
     // a step's charge change)
+    // Member buckets: 0..3 the envelope lines of shift d = bucket - 2, 4 any
+    // other shift, -1 none (infeasible, or in a bucket but off its envelope).
+    // Per class one pass counts the buckets (one byte each of a 64-bit word;
+    // a class has fewer than 256 members) and a second writes the lines.
+    auto member_bucket = [](const CtrlRec &r) -> int {
+        if (!r.ok)
+            return -1;
+        if (r.d >= -2 && r.d <= 1)
+            return r.ok == 2 ? r.d + 2 : -1;
+        return 4;
+    };
     int ent_carry = 0, spl_carry = 0, feas_carry = 0;
     for (int c0 = 0; c0 < P.n_cls; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
         Members mem = {};
-        int nspl = 0, nfeas = 0;
+        int nfeas = 0;
+        unsigned long long cnt = 0;  // byte q: lines of bucket q
         if (c < P.n_cls) {
             mem = class_members(P, c);
             const int b = c / (P.n_cls / P.n_b);
             for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
                 const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
                 const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
-                if (r.ok) {
-                    ++nfeas;
-                    ++nspl;
-                    if (r.d >= -2 && r.d <= 1 && r.ok != 2)
-                        --nspl;  // in a bucket but not on its envelope
-                }
+                nfeas += r.ok ? 1 : 0;
+                const int q = member_bucket(r);
+                if (q >= 0)
+                    cnt += 1ull << (8 * q);
             }
         }
+        // bytes 0..4 of `first`: the first line of each bucket, relative to the
+        // class (exclusive prefix sums of the counts; no byte carries, the sums
+        // stay below 256); byte 5: all lines of the class
+        const unsigned long long first = (cnt * 0x0101010101ull) << 8;
+        const int nspl = (int)((first >> 40) & 0xff);
         const int feas = nfeas > 0 ? 1 : 0;
         int ent_tot, spl_tot, feas_tot;
         const int ent_idx = block_exclusive_scan(feas, scan_buf, ent_tot) + ent_carry;
@@ -358,26 +373,22 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
             E.cls = c;
             E.off = spl_off;
             E.n_total = nspl;
-            int pos = spl_off;
-            for (int bucket = 0; bucket < 5; ++bucket) {
-                int cnt = 0;
-                for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
-                    const int im = member_im(mem, ie);
-                    const int u = (ie * P.n_tm + im) * P.n_b + b;
-                    const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
-                    const bool in4 = r.d >= -2 && r.d <= 1;
-                    if (bucket < 4 ? (r.ok != 2 || r.d != bucket - 2) : (!r.ok || in4))
-                        continue;
-                    const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(r.d & 0xffff) << 16);
-                    if (DP_IN(pos, P.n_u))
-                        spl_row[pos] = SplitRec{r.cost, r.f, bits, 0u};
-                    ++pos;
-                    ++cnt;
-                }
-                if (bucket < 4)
-                    E.nb[bucket] = cnt;
-                else
-                    E.n_other = cnt;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                E.nb[q] = (int)((cnt >> (8 * q)) & 0xff);
+            E.n_other = (int)((cnt >> 32) & 0xff);
+            unsigned long long next = first;  // byte q: next line of bucket q
+            for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
+                const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
+                const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
+                const int q = member_bucket(r);
+                if (q < 0)
+                    continue;
+                const int pos = spl_off + (int)((next >> (8 * q)) & 0xff);
+                next += 1ull << (8 * q);
+                const unsigned bits = (unsigned)(u & 0xffff) | ((unsigned)(r.d & 0xffff) << 16);
+                if (DP_IN(pos, P.n_u))
+                    spl_row[pos] = SplitRec{r.cost, r.f, bits, 0u};
             }
             if (DP_IN(ent_idx, P.n_cls))
                 ent_row[ent_idx] = E;
@@ -397,7 +408,8 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     }
 }
 
-__global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
+// 5 CTAs per SM: the shared-memory limit of the paper-scale control table
+__global__ void __launch_bounds__(256, 5) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
                                                          int k_first, StageScratch sc)
 {
     extern __shared__ __align__(16) unsigned char pre_smem[];
@@ -411,7 +423,7 @@ __global__ void __launch_bounds__(256) precompute_kernel(const DevParams *__rest
 
 // Batched: one CTA per (instance, stage, speed row); blocks of instance b
 // start at inst[b].row_off (rows of all its stages, stage-major).
-__global__ void __launch_bounds__(256) precompute_batched_kernel(const DevParams *__restrict__ params,
+__global__ void __launch_bounds__(256, 5) precompute_batched_kernel(const DevParams *__restrict__ params,
                                                                  const BatchInst *__restrict__ inst, int n_inst)
 {
     extern __shared__ __align__(16) unsigned char pre_smem[];
