@@ -62,9 +62,11 @@ struct dp_problem {
     SplitRec *d_spl = nullptr;
     float *d_pad_in = nullptr, *d_pad_out = nullptr, *d_dense = nullptr;
     // corner quads of J_k for the tiled sweep, two slots by stage parity
-    // (launch_quad_from_pad); padding entries hold V_BIG for the object's life
+    // (quad_rows x quad_ld per speed row, none when quad_ld is 0); entries
+    // outside the grid hold V_BIG for the object's life
     float4 *d_quad = nullptr;
-    float4 *quad(int k) const { return d_quad + (size_t)(k & 1) * stage_elems; }
+    size_t quad_elems = 0;
+    float4 *quad(int k) const { return d_quad ? d_quad + (size_t)(k & 1) * quad_elems : nullptr; }
     int16_t *d_pi_tmp = nullptr;
     double *d_roll = nullptr;
     int *d_roll_u = nullptr;
@@ -453,7 +455,8 @@ dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 {
     DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
     DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(p->N), s));
-    DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(p->N), p->quad(p->N), s));
+    if (p->d_quad)
+        DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(p->N), p->quad(p->N), s));
     DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, p->N, p->scratch(), s));
     for (int k = p->N - 1; k >= 0; --k)
         DP_CUDA(sweep_stage(p, k, s));
@@ -604,7 +607,9 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, rows * P.n_cls, &p->d_ent));
     TRY(dev_alloc_n(p, rows * 2, &p->d_rowcnt));
     TRY(dev_alloc_n(p, rows * P.n_u, &p->d_spl));
-    TRY(dev_alloc_n(p, 2 * p->stage_elems, &p->d_quad));
+    p->quad_elems = (size_t)P.n_v * quad_rows(P.n_xi) * quad_ld(P.n_t);
+    if (p->quad_elems > 0)
+        TRY(dev_alloc_n(p, 2 * p->quad_elems, &p->d_quad));
     TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_in));
     TRY(dev_alloc_n(p, p->stage_elems, &p->d_pad_out));
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_dense));
@@ -627,8 +632,9 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(cuda_try(cudaMemsetAsync(p->d_part, 0xff, p->pi_elems * sizeof(unsigned long long), p->create_stream),
                  "clear split minima"));
     // every padding cell holds the infeasible sentinel for the object's life
-    TRY(cuda_try(launch_fill(reinterpret_cast<float *>(p->d_quad), 8 * p->stage_elems, V_BIG, p->create_stream),
-                 "fill"));
+    if (p->d_quad)
+        TRY(cuda_try(launch_fill(reinterpret_cast<float *>(p->d_quad), 8 * p->quad_elems, V_BIG, p->create_stream),
+                     "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
@@ -797,7 +803,8 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
         DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
         DP_CUDA(cudaEventRecord(ev[0], s));
         DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(N), s));
-        DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(N), p->quad(N), s));
+        if (p->d_quad)
+            DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(N), p->quad(N), s));
         DP_CUDA(cudaEventRecord(ev[1], s));
         DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, N, p->scratch(), s));
         DP_CUDA(cudaEventRecord(ev[2], s));

@@ -29,10 +29,11 @@
 // of any other shift sit behind one warp-uniform test per class.  Two rows go
 // through one packed FP32 FMA (__ffma2_rn) and two lines through one
 // three-input min.  Two consecutive classes with the same speed cell and time
-// shift share the loads of their window.  In a single-problem sweep (QUAD)
-// the inner window rows come from corner quads of J_{k+1}, one 16-byte load
-// per row instead of four, and the epilogue writes J_k's quads for the next
-// stage.  Only class minima are tracked in
+// shift share the loads of their window.  In a single-problem sweep (QLD > 0)
+// the window rows come from corner quads of J_{k+1} (launch_quad_from_pad):
+// one 16-byte load per row instead of four, at compile-time offsets from one
+// address per class, and the epilogue writes J_k's quads for the next stage.
+// Only class minima are tracked in
 // the sweep; afterwards each warp buckets its states by winning class in
 // shared memory and re-evaluates that class (bit for bit the same arithmetic)
 // to recover the argmin.  An arrival during red points the class's time
@@ -103,6 +104,7 @@ __device__ __forceinline__ float blend(const float *p0, const float *p1, float w
 struct TCtx {
     const float *p0, *p1;  // speed rows iv, iv+1 of J_{k+1} at padded SoC row 0, lower time column
     float wv0, wv1, wt0, wt1;
+    int iv, ta;  // the speed cell and lower time column read
 };
 
 struct StageInfo {
@@ -166,6 +168,8 @@ __device__ __forceinline__ TCtx class_ctx_at(const DevParams &P, const float *Vn
     const size_t vrow = (size_t)P.xi_rows * P.ld_t;
     x.p0 = Vn + (size_t)iv * vrow + ta;
     x.p1 = x.p0 + vrow;
+    x.iv = iv;
+    x.ta = ta;
     return x;
 }
 
@@ -387,30 +391,32 @@ __device__ __forceinline__ float4 ldq(const float4 *p)
     return v;
 }
 
-// class_window and pair_window on the corner quads (q0: the quad of the
-// window's lower corner at padded SoC row 0): one load per window row, the
-// same blend.
-template <int R>
-__device__ __forceinline__ void class_window_q(const float4 *q0, const TCtx &x, const int (&roff)[R + 4],
-                                               float (&G)[R + 4])
+// Blend of one corner quad.
+__device__ __forceinline__ float blend_quad(const float4 c, float wv0, float wv1, float wt0, float wt1)
 {
-#pragma unroll
-    for (int w = 1; w < R + 3; ++w) {
-        const float4 c = ldq(q0 + roff[w]);
-        G[w] = blend_raw(make_float2(c.x, c.y), make_float2(c.z, c.w), x.wv0, x.wv1, x.wt0, x.wt1);
-    }
+    return blend_raw(make_float2(c.x, c.y), make_float2(c.z, c.w), wv0, wv1, wt0, wt1);
 }
 
-template <int R>
-__device__ __forceinline__ void pair_window_q(const float4 *q0, const TCtx &x, const int (&roff)[R + 4], float bv0,
-                                              float bv1, float bt0, float bt1, float (&G)[R + 4], float (&H)[R + 4])
+// class_window and pair_window on the corner quads: q0 is the quad of the
+// window's row w = 0 (SoC row jb - 2), row w sits QLD quads further, a
+// compile-time offset.
+template <int R, int QLD>
+__device__ __forceinline__ void class_window_q(const float4 *q0, const TCtx &x, float (&G)[R + 4])
+{
+#pragma unroll
+    for (int w = 1; w < R + 3; ++w)
+        G[w] = blend_quad(ldq(q0 + w * QLD), x.wv0, x.wv1, x.wt0, x.wt1);
+}
+
+template <int R, int QLD>
+__device__ __forceinline__ void pair_window_q(const float4 *q0, const TCtx &x, float bv0, float bv1, float bt0,
+                                              float bt1, float (&G)[R + 4], float (&H)[R + 4])
 {
 #pragma unroll
     for (int w = 1; w < R + 3; ++w) {
-        const float4 c = ldq(q0 + roff[w]);
-        const float2 lo = make_float2(c.x, c.y), hi = make_float2(c.z, c.w);
-        G[w] = blend_raw(lo, hi, x.wv0, x.wv1, x.wt0, x.wt1);
-        H[w] = blend_raw(lo, hi, bv0, bv1, bt0, bt1);
+        const float4 c = ldq(q0 + w * QLD);
+        G[w] = blend_quad(c, x.wv0, x.wv1, x.wt0, x.wt1);
+        H[w] = blend_quad(c, bv0, bv1, bt0, bt1);
     }
 }
 
@@ -567,7 +573,7 @@ __device__ __forceinline__ unsigned long long pack_min(float v, int e)
     return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)e;
 }
 
-template <int R, bool NC, int MODE = TILE_FULL, bool QUAD = false>
+template <int R, bool NC, int MODE = TILE_FULL, int QLD = 0>
 __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, const ClassRec *g_cls,
                              const ClassEntry *g_ent, const SplitRec *g_spl, int n_ent, int n_spl, const float *Vn,
                              float *__restrict__ Vk, int16_t *__restrict__ pik, int i, int chunk,
@@ -633,6 +639,11 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
 #pragma unroll
     for (int w = 0; w < R + 4; ++w)
         roff[w] = row_offset(P, jb - 2 + w);
+    // corner quads (QLD > 0): the lane's window row w = 0 (SoC row jb - 2) is
+    // quad row jb - 2 + QUAD_PAD of every speed row
+    const int qrows = quad_rows(P.n_xi);
+    const size_t vrowq = (size_t)qrows * QLD;
+    const float4 *qlane = QLD > 0 ? Qn + (size_t)(jb - 2 + QUAD_PAD) * QLD : nullptr;
 
     // per row: the running minimum and the first class (in class order)
     // reaching it (the order (value, class, control) decides exact ties)
@@ -677,13 +688,12 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                 T2 = s_tc[e + 1];
                 have_h = T2.ivst == T.ivst;
             }
-            if (QUAD) {
-                // the quad at the same flat index as the window's lower corner
-                const float4 *q0 = Qn + (x.p0 - Vn);
+            if (QLD > 0) {
+                const float4 *q0 = qlane + (size_t)x.iv * vrowq + x.ta;
                 if (have_h)
-                    pair_window_q<R>(q0, x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft, G, H);
+                    pair_window_q<R, QLD>(q0, x, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft, G, H);
                 else
-                    class_window_q<R>(q0, x, roff, G);
+                    class_window_q<R, QLD>(q0, x, G);
             } else if (have_h) {
                 pair_window<R, NC>(x, roff, __fsub_rn(1.f, T2.fv), T2.fv, __fsub_rn(1.f, T2.ft), T2.ft, G, H);
             } else {
@@ -722,8 +732,14 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         // any other shift
         if ((T.nb0 | (int)T.nb3_other) != 0) {  // nb[0], nb[3] or n_other
             const TCtx x = tile_ctx(P, Vn, T, s_dtv, e, l, tl, wait, si);
-            G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
-            G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
+            if (QLD > 0) {
+                const float4 *q0 = qlane + (size_t)x.iv * vrowq + x.ta;
+                G[0] = blend_quad(ldq(q0), x.wv0, x.wv1, x.wt0, x.wt1);
+                G[R + 3] = blend_quad(ldq(q0 + (R + 3) * QLD), x.wv0, x.wv1, x.wt0, x.wt1);
+            } else {
+                G[0] = blend<NC>(x.p0 + roff[0], x.p1 + roff[0], x.wv0, x.wv1, x.wt0, x.wt1);
+                G[R + 3] = blend<NC>(x.p0 + roff[R + 3], x.p1 + roff[R + 3], x.wv0, x.wv1, x.wt0, x.wt1);
+            }
             Dg[0] = __fsub_rn(G[1], G[0]);
             Dg[R + 2] = __fsub_rn(G[R + 3], G[R + 2]);
             EV[0] = make_float2(Dg[0], Dg[1]);
@@ -785,16 +801,20 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             Vk[ov] = val;
             if (!feas)
                 pik[op] = -1;
-            if (QUAD) {
-                // J_k's value in the four quads that hold it (ov >= ld_t: the
-                // state sits below padding row -1; speed row i - 1 from i > 0)
+            if (QLD > 0) {
+                // J_k's value in the quads that hold it: (i, j, l).x,
+                // (i, j, l - 1).y, (i - 1, j, l).z, (i - 1, j, l - 1).w
                 float *qf = reinterpret_cast<float *>(Qk);
-                const size_t vrow = (size_t)P.xi_rows * P.ld_t;
-                qf[4 * ov] = val;
-                qf[4 * (ov - 1) + 1] = val;
-                if (i > 0) {
-                    qf[4 * (ov - vrow) + 2] = val;
-                    qf[4 * (ov - vrow - 1) + 3] = val;
+                const size_t oq = ((size_t)i * qrows + (j + QUAD_PAD)) * QLD + l;
+                if (DP_IN(oq, (size_t)P.n_v * vrowq)) {
+                    qf[4 * oq] = val;
+                    if (l > 0)
+                        qf[4 * (oq - 1) + 1] = val;
+                    if (i > 0) {
+                        qf[4 * (oq - vrowq) + 2] = val;
+                        if (l > 0)
+                            qf[4 * (oq - vrowq - 1) + 3] = val;
+                    }
                 }
             }
         }

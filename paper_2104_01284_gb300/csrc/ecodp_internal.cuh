@@ -337,16 +337,32 @@ cudaError_t launch_terminal(const DevParams *dP, const DevParams &hP, float *VN,
 // Tables of stages k_first .. k_first + n_k - 1 (one CTA per speed row and stage).
 cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTables tb, int k_first, int n_k,
                               StageScratch sc, cudaStream_t s);
-// Corner quads of a padded value array: Q[q] = {V[q], V[q + 1], V[q + vrow],
-// V[q + vrow + 1]} for every flat index q of the padded layout (vrow =
-// xi_rows ld_t, one speed row; entries past the array read V_BIG), i.e. the
-// two time columns of a cell at speed rows iv and iv + 1.  A Bellman tile
-// reads a window row of J_{k+1} with one 16-byte load instead of four.
+// Corner quads of J for the tiled sweep: quad (iv, j, c) = {V(iv, j, c),
+// V(iv, j, c + 1), V(iv + 1, j, c), V(iv + 1, j, c + 1)}, the two time columns
+// of a cell at speed rows iv and iv + 1 in one 16-byte record, with V = V_BIG
+// outside the grid (j < 0 or j >= n_soc, c >= n_t, iv >= n_v).  Layout
+// [n_v][quad_rows][quad_ld], SoC row j at quad row j + 2: every window row a
+// tile of 6 or 8 SoC rows per lane reads (SoC rows jb - 2 .. jb + R + 1) lies
+// inside, so a window row is a compile-time offset from one address (no
+// clamping), and quad_ld, a row stride the kernel is compiled for, is the
+// smallest of 64, 128, 256 that holds n_t + 2 columns (0: no quads, the
+// plain layout is read).
+constexpr int QUAD_PAD = 2;  // quad rows below SoC row 0
+__host__ __device__ inline int quad_rows(int n_xi)
+{
+    const int r6 = (n_xi + 5) / 6 * 6, r8 = (n_xi + 7) / 8 * 8;
+    return (r6 > r8 ? r6 : r8) + 2 * QUAD_PAD;
+}
+__host__ __device__ inline int quad_ld(int n_t)
+{
+    return n_t + 2 <= 64 ? 64 : (n_t + 2 <= 128 ? 128 : (n_t + 2 <= 256 ? 256 : 0));
+}
+// Quads of a padded value array (J_N of a sweep).
 cudaError_t launch_quad_from_pad(const DevParams &hP, const float *V, float4 *Q, cudaStream_t s);
 // One Bellman stage.  With Qn and Qk (corner quads of J_{k+1} and J_k, the
-// latter written by the launch) the tiled kernel reads its windows from Qn;
-// every other path ignores them, so a sweep must pass them at every stage or
-// at none.
+// latter written by the launch) the unsplit tiled kernel reads its windows
+// from Qn; every other path ignores them, so a sweep must pass them at every
+// stage or at none.
 cudaError_t launch_bellman(const DevParams *dP, const DevParams &hP, StageTables tb, int k, StageScratch sc,
                            const float *Vnext, float *Vk, int16_t *pik, int variant, cudaStream_t s,
                            const float4 *Qn = nullptr, float4 *Qk = nullptr);

@@ -84,9 +84,9 @@ __global__ void __launch_bounds__(256) bellman_direct(const DevParams *__restric
     }
 }
 
-// QUAD: windows read from the corner quads Qn of J_{k+1}, J_k's quads written
-// to Qk (a sweep whose every stage takes this kernel).
-template <int R, bool QUAD>
+// QLD > 0: windows read from the corner quads Qn of J_{k+1} (row stride QLD),
+// J_k's quads written to Qk (a sweep whose every stage takes this kernel).
+template <int R, int QLD>
 __global__ void __launch_bounds__(TLANES, tile_minb<R>())
     bellman_tiled(const DevParams *__restrict__ dP, StageTables tb, int k, StageScratch sc,
                   const float *__restrict__ Vn, float *__restrict__ Vk, int16_t *__restrict__ pik,
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(TLANES, tile_minb<R>())
     // come last and fill the SMs that received a fourth CTA
     const int i = gridDim.y - 1 - blockIdx.y;
     const size_t row = (size_t)k * P.n_v + i;
-    bellman_tile<R, true, TILE_FULL, QUAD>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
+    bellman_tile<R, true, TILE_FULL, QLD>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
                                            sc.spl + row * P.n_u, sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn,
                                            Vk, pik, i, blockIdx.x, smem_raw, sc.stats, 0, 0, nullptr, Qn, Qk);
 }
@@ -229,21 +229,24 @@ cudaError_t launch_tiles(const DevParams *dP, const DevParams &hP, StageTables t
         bellman_join<<<dim3((hP.n_xi * hP.n_t + 255) / 256, hP.n_v), 256, 0, s>>>(dP, tb, k, sc, Vnext, Vk, pik);
         return cudaGetLastError();
     }
-    if (Qn && Qk) {
-        cudaError_t err =
-            cudaFuncSetAttribute(bellman_tiled<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int qld = Qn && Qk ? quad_ld(hP.n_t) : 0;
+    auto run = [&](auto kernel) {
+        cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return err;
-        bellman_tiled<R, true><<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
+        kernel<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
         return cudaGetLastError();
+    };
+    switch (qld) {
+    case 64:
+        return run(bellman_tiled<R, 64>);
+    case 128:
+        return run(bellman_tiled<R, 128>);
+    case 256:
+        return run(bellman_tiled<R, 256>);
+    default:
+        return run(bellman_tiled<R, 0>);
     }
-    cudaError_t err =
-        cudaFuncSetAttribute(bellman_tiled<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess)
-        return err;
-    bellman_tiled<R, false><<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, nullptr,
-                                                                        nullptr);
-    return cudaGetLastError();
 }
 
 }  // namespace

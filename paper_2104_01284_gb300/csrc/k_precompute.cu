@@ -76,17 +76,30 @@ __global__ void dense_from_pad_kernel(const DevParams P, const float *__restrict
     }
 }
 
+// J(iv, j, c) of a padded value array, V_BIG outside the grid.
+__device__ __forceinline__ float grid_value(const DevParams &P, const float *V, int iv, int j, int c)
+{
+    if (iv < 0 || iv >= P.n_v || j < 0 || j >= P.n_xi || c < 0 || c >= P.n_t)
+        return V_BIG;
+    const size_t o = ((size_t)iv * P.xi_rows + (j + 1)) * P.ld_t + c;
+    return DP_IN(o, (size_t)P.n_v * P.xi_rows * P.ld_t) ? V[o] : V_BIG;
+}
+
 // Corner quads of a padded value array (launch_quad_from_pad).
 __global__ void quad_from_pad_kernel(const DevParams P, const float *__restrict__ V, float4 *__restrict__ Q)
 {
-    const size_t vrow = (size_t)P.xi_rows * P.ld_t;
+    const int rows = quad_rows(P.n_xi), ld = quad_ld(P.n_t);
+    const size_t vrow = (size_t)rows * ld;
     const size_t total = (size_t)P.n_v * vrow;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const int iv = (int)(q / vrow);
+        const int rem = (int)(q - (size_t)iv * vrow);
+        const int j = rem / ld - QUAD_PAD, c = rem % ld;
         float4 r;
-        r.x = V[q];
-        r.y = q + 1 < total ? V[q + 1] : V_BIG;
-        r.z = q + vrow < total ? V[q + vrow] : V_BIG;
-        r.w = q + vrow + 1 < total ? V[q + vrow + 1] : V_BIG;
+        r.x = grid_value(P, V, iv, j, c);
+        r.y = grid_value(P, V, iv, j, c + 1);
+        r.z = grid_value(P, V, iv + 1, j, c);
+        r.w = grid_value(P, V, iv + 1, j, c + 1);
         Q[q] = r;
     }
 }
@@ -532,7 +545,9 @@ cudaError_t launch_pad_from_dense(const DevParams &hP, const float *dense, float
 
 cudaError_t launch_quad_from_pad(const DevParams &hP, const float *V, float4 *Q, cudaStream_t s)
 {
-    const size_t total = (size_t)hP.n_v * hP.xi_rows * hP.ld_t;
+    if (quad_ld(hP.n_t) == 0)
+        return cudaSuccess;  // no quads for this time grid
+    const size_t total = (size_t)hP.n_v * quad_rows(hP.n_xi) * quad_ld(hP.n_t);
     const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     quad_from_pad_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(hP, V, Q);
     return cudaGetLastError();

@@ -106,16 +106,17 @@ def test_tiled_and_direct_bit_identical(gpu, name):
         a.close()
 
 
-@pytest.mark.parametrize("variant", ["tiled", "tiled6"])
-def test_unsplit_tiled_sweep_bit_identical(gpu, variant):
+@pytest.mark.parametrize("variant,n_t", [("tiled", 201), ("tiled6", 201), ("tiled", 101), ("tiled", 45)])
+def test_unsplit_tiled_sweep_bit_identical(gpu, variant, n_t):
     """A grid with enough tiles for the unsplit tiled kernel (more than half
     of the GPU's resident CTA slots, 4 per SM), whose sweep reads J_{k+1}
-    through the corner quads the previous stage wrote: every J_k and pi_k of
-    the sweep equals, bit for bit, the stage hook (plain loads of J_{k+1}) run
-    on the sweep's own J_{k+1}, and the direct kernel's sweep.  Two lights
-    cover the unpaired window loads of light stages."""
+    through the corner quads the previous stage wrote (row strides 256, 128
+    and 64 for 201, 101 and 45 time points): every J_k and pi_k of the sweep
+    equals, bit for bit, the stage hook (plain loads of J_{k+1}) run on the
+    sweep's own J_{k+1}, and the direct kernel's sweep.  Two lights cover the
+    unpaired window loads of light stages."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    n_soc, n_t, R = 51, 201, (8 if variant == "tiled" else 6)
+    n_soc, R = 51, (8 if variant == "tiled" else 6)
     chunks = (-(-n_soc // R) * n_t + 127) // 128
     n_v = max(31, 2 * sms // chunks + 1)
     assert n_v * chunks > 2 * sms  # the class-split launch is not taken
