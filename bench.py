@@ -38,10 +38,10 @@ FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample e
 # dram__bytes_read.sum + dram__bytes_write.sum of one Bellman launch (stage 79
 # of this workload) from an ncu capture of the current kernel version (ncu's
 # counters cannot be read inside a timed run; ncu empties the caches before
-# the launch, so J_{k+1}'s corner quads, 8.8 MB, come from DRAM there, while
+# the launch, so J_{k+1}'s corner quads, 12.5 MB, come from DRAM there, while
 # in the sweep the previous launch has just written them to L2).  None
 # whenever the kernel has changed since the last capture.
-BELLMAN_TRAFFIC_BYTES = 12.186368e6
+BELLMAN_TRAFFIC_BYTES = 13.375488e6
 
 
 def parse():
