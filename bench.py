@@ -41,7 +41,7 @@ FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample e
 # the launch, so J_{k+1}'s corner quads, 12.5 MB, come from DRAM there, while
 # in the sweep the previous launch has just written them to L2).  None
 # whenever the kernel has changed since the last capture.
-BELLMAN_TRAFFIC_BYTES = 13.375488e6
+BELLMAN_TRAFFIC_BYTES = 13.398528e6
 
 
 def parse():
@@ -484,7 +484,7 @@ def run_ours(args):
     per_launch_s = bell_ms / 1e3 / p.n_stages
     # per (state, envelope line): 1 FMA; per (state, torque class): three
     # two-way blends of J_{k+1} (9 FLOP), the SoC-row difference and the add
-    flops_per_launch = (2.0 * stats["envelope_evals"] + 11.0 * stats["class_evals"]) / p.n_stages
+    flops_per_launch = (2.0 * stats["envelope_evals"] + 9.0 * stats["class_evals"]) / p.n_stages
     achieved = flops_per_launch / per_launch_s / 1e12
     # FP32 FMA peak from the device's SM count and the SM clock sampled
     # during the timed region
@@ -496,7 +496,7 @@ def run_ours(args):
                 "traffic": BELLMAN_TRAFFIC_BYTES,
                 "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {mhz:.0f} MHz "
                               f"({'median sampled SM clock' if clocks.get('sm_mhz') else 'maximum SM clock'})",
-                "work_basis": "2 FLOP per (state, envelope line) FMA + 11 FLOP per (state, torque class) window value",
+                "work_basis": "2 FLOP per (state, envelope line) FMA + 9 FLOP per (state, torque class) window value (bilinear blend of 4 corners: 4 mul + 3 add, the SoC difference, the add)",
                 "bellman_ms_per_launch": 1e3 * per_launch_s,
                 "share_of_sweep": bell_ms / sweep_ms if sweep_ms > 0 else None,
                 "precompute_ms_per_launch": pre_ms / p.n_stages,

@@ -83,13 +83,17 @@ __device__ __forceinline__ float ldv(const float *p)
     return __ldca(p);
 }
 
-// Speed blend of the two time columns as one packed multiply and one packed
-// FMA (per lane the same IEEE operations as the scalar form
-// A = wv1 p1 + (wv0 p0)), then the time blend G = wt1 B + (wt0 A).
+// Bilinear blend of a cell's four corners (lo: the lower speed row's two time
+// columns, hi: the upper's) with the weights (wt0 wv0, wt1 wv0) on lo and
+// (wt0 wv1, wt1 wv1) on hi: one packed multiply, one packed FMA and one add
+// per value.  The weight products depend on the class only, so a window's
+// rows share them.
 __device__ __forceinline__ float blend_raw(float2 lo, float2 hi, float wv0, float wv1, float wt0, float wt1)
 {
-    const float2 AB = __ffma2_rn(make_float2(wv1, wv1), hi, __fmul2_rn(make_float2(wv0, wv0), lo));
-    return __fmaf_rn(wt1, AB.y, __fmul_rn(wt0, AB.x));
+    const float2 w0 = __fmul2_rn(make_float2(wt0, wt1), make_float2(wv0, wv0));
+    const float2 w1 = __fmul2_rn(make_float2(wt0, wt1), make_float2(wv1, wv1));
+    const float2 S = __ffma2_rn(w1, hi, __fmul2_rn(w0, lo));
+    return __fadd_rn(S.x, S.y);
 }
 
 template <bool NC>
