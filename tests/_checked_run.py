@@ -20,6 +20,18 @@ from tests.test_gpu_parity import PROBLEMS  # noqa: E402
 from tests.test_gpu_variants import VARIANTS  # noqa: E402
 
 
+UNSPLIT = {
+    "unsplit": P.config1(seed=77, n_stages=6, n_v=31, n_soc=51, n_t=201, n_te=11, n_tm=11, n_lights=2, t_hi=60.0),
+    "unsplit_t101": P.config1(seed=77, n_stages=6, n_v=51, n_soc=51, n_t=101, n_te=11, n_tm=11, n_lights=2,
+                              t_hi=60.0),
+}
+
+
+def j0_hash(dp):
+    import hashlib
+    return hashlib.sha1(dp.value(0).cpu().numpy().astype(np.float32).tobytes()).hexdigest()
+
+
 def clean(phase, done):
     en, site = N.debug_checks()
     assert en, "the checked library is not loaded"
@@ -32,13 +44,19 @@ def main():
     done, digest = [], {}
     probs = {"c0": P.config0(), "reduced": PROBLEMS["reduced"](), "wide_shift": PROBLEMS["wide_shift"](),
              "paper_grid": P.paper_table1(), "literal": VARIANTS["literal"](), "both": VARIANTS["both"]()}
+    # grids with enough tiles for the unsplit tiled kernel and its corner
+    # quads (row strides 256 and 128); J_0 reported as a hash
+    probs.update(UNSPLIT)
+    hashes = {}
     for name, p in probs.items():
         for variant in ("tiled", "direct"):
             dp = EcoDP(p)
             dp.set_variant(variant)
             dp.solve()
             clean(f"{name}/{variant}/sweep", done)
-            if variant == "tiled":
+            if variant == "tiled" and name in UNSPLIT:
+                hashes[name] = j0_hash(dp)
+            elif variant == "tiled":
                 digest[name] = np.asarray(dp.value(0).cpu().numpy(), np.float64).tolist()
                 dp.rollout(raise_infeasible=False)
                 clean(f"{name}/rollout", done)
@@ -78,7 +96,7 @@ def main():
         bt.wait()
         bt.rollout(raise_infeasible=False)
         clean("batch", done)
-    print(json.dumps({"phases": done, "digest": digest}))
+    print(json.dumps({"phases": done, "digest": digest, "hashes": hashes}))
 
 
 if __name__ == "__main__":

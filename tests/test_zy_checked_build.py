@@ -1,6 +1,7 @@
 """The bounds-checked build (libecodp_checked.so, -DECODP_CHECKS) on the GPU:
 the tiny and reduced problems, the paper's Table I grid, two paper variants,
-a checkpointed adjoint and a 4-instance batch run through it in a child
+two grids large enough for the unsplit tiled kernel with corner quads, a
+checkpointed adjoint and a 4-instance batch run through it in a child
 process (the binding loads one library per process), and the device's
 bounds-check record stays empty after every phase.  The checks change no
 arithmetic: J_0 equals the production build's bit for bit."""
@@ -41,3 +42,9 @@ def test_checked_build_records_no_bounds_failure():
     dp.solve()
     assert np.array_equal(np.asarray(out["digest"]["c0"]), dp.value(0).cpu().numpy().astype(np.float64))
     dp.close()
+    from tests._checked_run import UNSPLIT, j0_hash
+    for name, p in UNSPLIT.items():
+        dp = EcoDP(p)
+        dp.solve()
+        assert out["hashes"][name] == j0_hash(dp), name
+        dp.close()
