@@ -1,5 +1,6 @@
 """Paper-scale end-to-end parity: the full 100-stage backward sweep and the
-rollout on the GPU against the FP64 oracle's stored results.
+rollout on the GPU against the FP64 oracle's stored results, on every
+paper-scale instance (seed) with a stored oracle sweep.
 
 The oracle's sweep of this instance (1e11 state x control evaluations) takes
 tens of CPU-core-hours, so `tests/golden/make_c1_golden.py` (which calls only
@@ -18,26 +19,24 @@ from tests._parity import compare
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore")]
 
 torch = pytest.importorskip("torch")
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c1_s1.npz")
+GOLDEN_DIR = os.path.join(os.path.dirname(__file__), "golden")
+SEEDS = (1, 2)  # paper-scale instances with a stored oracle sweep
 
 
-@pytest.fixture(scope="module")
-def golden():
-    if not os.path.exists(GOLDEN):
-        pytest.skip("golden file not generated")
-    return dict(np.load(GOLDEN))
-
-
-@pytest.fixture(scope="module")
-def solved():
+@pytest.fixture(scope="module", params=SEEDS)
+def case(request):
+    seed = request.param
+    path = os.path.join(GOLDEN_DIR, f"c1_s{seed}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"golden file for seed {seed} not generated")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2104_01284_gb300.solver import EcoDP
-    p = P.config1(seed=1)
+    p = P.config1(seed=seed)
     dp = EcoDP(p)
     dp.solve()
     torch.cuda.synchronize()
-    yield p, dp
+    yield seed, dict(np.load(path)), p, dp
     dp.close()
 
 
@@ -46,14 +45,14 @@ def _mask(g, name, k, n):
 
 
 @pytest.mark.parametrize("k", [99, 50, 0])
-def test_paper_scale_masks_and_values(golden, solved, k):
+def test_paper_scale_masks_and_values(case, k):
     """Full-grid masks and sampled values/policies at stages 99, 50 and 0.
     Coverage is part of the check: at least 90 % of the sampled feasible
     states get the 1e-4 value check and at least 80 % of the decisive ones
     (oracle gap above 1e-4) the policy check; excused mask flips stay below
     1 % of the feasible states.  The counts are printed in the session's
     parity summary."""
-    p, dp = solved
+    seed, golden, p, dp = case
     n = p.n_states
     gV = dp.value(k).cpu().numpy().astype(np.float64).ravel()
     m_nom, m_lo, m_hi = (_mask(golden, nm, k, n) for nm in ("nom", "lo", "hi"))
@@ -68,7 +67,7 @@ def test_paper_scale_masks_and_values(golden, solved, k):
     idx = golden[f"idx_k{k}"]
     gp = dp.policy(k).cpu().numpy().ravel()[idx]
     st = compare(gV[idx], gp, golden[f"V_nom_k{k}"], golden[f"V_lo_k{k}"], golden[f"V_hi_k{k}"],
-                 golden[f"pi_k{k}"], golden[f"sec_k{k}"], where=f"c1/e2e/k{k}")
+                 golden[f"pi_k{k}"], golden[f"sec_k{k}"], where=f"c1/e2e/s{seed}/k{k}")
     st["mask_exceptions_full_grid"] = int(excused.sum())
     st["feasible_full_grid"] = int(m_nom.sum())
     print(f"k={k}: mask exceptions {int(excused.sum())} of {int(m_nom.sum())} feasible; sample {st}")
@@ -76,8 +75,8 @@ def test_paper_scale_masks_and_values(golden, solved, k):
     assert st["policy_checked"] >= 0.8 * st["decisive"], st
 
 
-def test_paper_scale_rollout(golden, solved):
-    p, dp = solved
+def test_paper_scale_rollout(case):
+    seed, golden, p, dp = case
     assert int(golden["roll_status"]) == 0
     r = dp.rollout()
     assert r["status"] == 0
