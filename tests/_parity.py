@@ -71,10 +71,13 @@ def compare(gpu_V, gpu_pi, nom, lo, hi, pi_nom=None, second=None, rtol=RTOL, ato
             f"{where}: {int(bad_i.sum())} values outside the fragile interval at "
             f"{np.argwhere(bad_i)[:5].tolist()} gpu={gV[bad_i][:5]} lo={lo[bad_i][:5]} hi={hi[bad_i][:5]}")
     n_feas = int(fn.sum())
+    # relative error on the checked states with a nonzero oracle value (a zero
+    # value is held to the absolute tolerance)
+    nz = tight & (nom != 0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        max_rel = float(np.max(err[nz] / np.abs(nom[nz]))) if nz.any() else 0.0
     stats = dict(where=where, states=int(gV.size), feasible=n_feas, mask_exceptions=int(excused.sum()),
-                 loose=int((fn & ~tight).sum()), value_checked=int(tight.sum()),
-                 max_rel_err=float(np.max(np.where(err[tight] == 0, 0.0, err[tight] / np.abs(nom[tight]))))
-                 if tight.any() else 0.0)
+                 loose=int((fn & ~tight).sum()), value_checked=int(tight.sum()), max_rel_err=max_rel)
     # (c) policy
     if gpu_pi is not None and pi_nom is not None and second is not None:
         gp = np.asarray(gpu_pi).astype(np.int64)
