@@ -176,7 +176,11 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
  * J_1..J_N: at each stage every control is evaluated at the continuous
  * state, the argmin (lowest index on ties) is applied, and fuel and time are
  * summed in FP64 on the device.  Fills the caller's host trajectory and
- * synchronises the stream.  DP_ERR_INFEASIBLE if a stage has no feasible
+ * synchronises the stream.  Called right after dp_solve_backward on the same
+ * stream (no other call on the problem in between, no checkpointing), the
+ * rollout starts as soon as J_1 is written, beside the sweep's last stage,
+ * on a stream of the problem's own that the caller's stream then waits for;
+ * the result is the same.  DP_ERR_INFEASIBLE if a stage has no feasible
  * control (traj->fail_stage tells which); DP_ERR_NOT_SOLVED before a solve. */
 dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, void *stream);
 

@@ -87,6 +87,14 @@ struct dp_problem {
     bool solved = false;
     int variant = 1;
     cudaStream_t cap_stream = nullptr;
+    // A dp_rollout that follows the solve on its stream (no other call on the
+    // problem in between) needs J_1 .. J_N only: the sweep records ev_stage1
+    // once J_1 is written, the rollout runs on roll_stream from there while
+    // the last Bellman stage finishes, and the caller's stream waits for it.
+    cudaEvent_t ev_stage1 = nullptr, ev_rolled = nullptr;
+    cudaStream_t roll_stream = nullptr;
+    cudaStream_t solve_stream = nullptr;
+    bool rollout_may_overlap = false;
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
 
@@ -345,6 +353,16 @@ void release(dp_problem *p)
     if (p->cap_stream)
         cudaStreamDestroy(p->cap_stream);
     p->cap_stream = nullptr;
+    if (p->roll_stream) {
+        cudaStreamSynchronize(p->roll_stream);
+        cudaStreamDestroy(p->roll_stream);
+    }
+    p->roll_stream = nullptr;
+    if (p->ev_stage1)
+        cudaEventDestroy(p->ev_stage1);
+    if (p->ev_rolled)
+        cudaEventDestroy(p->ev_rolled);
+    p->ev_stage1 = p->ev_rolled = nullptr;
     if (!p->blocks.empty())
         cudaStreamSynchronize(p->create_stream);
     for (void *b : p->blocks) {
@@ -458,8 +476,11 @@ dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
     if (p->d_quad)
         DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(p->N), p->quad(p->N), s));
     DP_CUDA(launch_precompute(p->dP, p->hP, p->tables(), 0, p->N, p->scratch(), s));
-    for (int k = p->N - 1; k >= 0; --k)
+    for (int k = p->N - 1; k >= 0; --k) {
         DP_CUDA(sweep_stage(p, k, s));
+        if (k == 1)  // J_1 .. J_N complete (an event node of the graph when captured)
+            DP_CUDA(cudaEventRecordWithFlags(p->ev_stage1, s, cudaEventRecordExternal));
+    }
     return DP_OK;
 }
 
@@ -470,8 +491,19 @@ namespace host {
 
 size_t roll_doubles(int N) { return (size_t)(3 * (N + 1) + 3 * N + 4); }
 
-dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s)
+dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s, bool overlap)
 {
+    if (overlap && p->rollout_may_overlap && s == p->solve_stream && p->n_segments() == 1) {
+        // from J_1 on, beside the sweep's last stage (the rollout never reads J_0)
+        DP_CUDA(cudaStreamWaitEvent(p->roll_stream, p->ev_stage1, 0));
+        DP_CUDA(launch_rollout(p->dP, p->hP, p->tables(), p->seg_view(0), 0, p->N, x0[0], x0[1], x0[2], p->d_roll,
+                               p->d_roll_u, p->roll_stream));
+        DP_CUDA(cudaEventRecord(p->ev_rolled, p->roll_stream));
+        DP_CUDA(cudaStreamWaitEvent(s, p->ev_rolled, 0));
+        DP_CUDA(cudaMemcpyAsync(h_out, p->d_roll, roll_doubles(p->N) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DP_CUDA(cudaMemcpyAsync(h_u, p->d_roll_u, (size_t)p->N * sizeof(int), cudaMemcpyDeviceToHost, s));
+        return DP_OK;
+    }
     for (int c = 0; c < p->n_segments(); ++c) {
         dp_status st = recompute_segment(p, c, s);
         if (st != DP_OK)
@@ -638,6 +670,9 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(cuda_try(launch_fill(p->d_pad_in, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(launch_fill(p->d_pad_out, p->stage_elems, V_BIG, p->create_stream), "fill"));
     TRY(cuda_try(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
+    TRY(cuda_try(cudaStreamCreateWithFlags(&p->roll_stream, cudaStreamNonBlocking), "cudaStreamCreate"));
+    TRY(cuda_try(cudaEventCreateWithFlags(&p->ev_stage1, cudaEventDisableTiming), "cudaEventCreate"));
+    TRY(cuda_try(cudaEventCreateWithFlags(&p->ev_rolled, cudaEventDisableTiming), "cudaEventCreate"));
     size_t smem = bellman_smem_bytes(P);
     if (smem > 227 * 1024) {
         release(p);
@@ -669,6 +704,7 @@ dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *s
     fill_tables(desc, p->h);
     st = upload_tables(p, (cudaStream_t)stream);
     p->solved = false;
+    p->rollout_may_overlap = false;
     return st;
 }
 
@@ -727,6 +763,7 @@ dp_status dp_set_checkpointing(dp_problem_t p, int32_t every)
     DP_CUDA(cudaDeviceSynchronize());
     free_value_storage(p);
     p->ckpt = K;
+    p->rollout_may_overlap = false;
     if (p->gexec)
         cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
@@ -757,11 +794,14 @@ dp_status dp_solve_backward(dp_problem_t p, void *stream)
     if (!p)
         return fail(DP_ERR_INVALID_ARG, "problem is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    p->rollout_may_overlap = false;
     if (!p->use_graph) {
         dp_status st = enqueue_sweep(p, s);
         if (st != DP_OK)
             return st;
         p->solved = true;
+        p->solve_stream = s;
+        p->rollout_may_overlap = p->N >= 2 && p->ckpt == 0;
         return DP_OK;
     }
     if (!p->gexec) {
@@ -785,6 +825,8 @@ dp_status dp_solve_backward(dp_problem_t p, void *stream)
     }
     DP_CUDA(cudaGraphLaunch(p->gexec, s));
     p->solved = true;
+    p->solve_stream = s;
+    p->rollout_may_overlap = p->N >= 2 && p->ckpt == 0;
     return DP_OK;
 }
 
@@ -793,6 +835,7 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
     NvtxRange nvtx_("ecodp.profile_sweep");
     if (!p || !ms)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
+    p->rollout_may_overlap = false;
     cudaStream_t s = (cudaStream_t)stream;
     const int N = p->N;
     std::vector<cudaEvent_t> ev(N + 3, nullptr);
@@ -882,6 +925,8 @@ dp_status dp_get_policy(dp_problem_t p, int32_t stage, int16_t *out, int32_t out
 dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t v_next_is_host, float *v_out,
                          int16_t *pi_out, int32_t out_is_host, void *stream)
 {
+    if (p)
+        p->rollout_may_overlap = false;
     if (!p || !v_next)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (k < 0 || k >= p->N)
@@ -910,6 +955,8 @@ dp_status dp_solve_stage(dp_problem_t p, int32_t k, const float *v_next, int32_t
 
 static dp_status adjoint_impl(dp_problem_t p, const double x0[3], double dJ_dtheta[5], double *J0, void *stream)
 {
+    if (p)
+        p->rollout_may_overlap = false;
     if (!p || !x0 || !dJ_dtheta)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!finite_all({x0[0], x0[1], x0[2]}))
@@ -957,7 +1004,7 @@ static dp_status rollout_impl(dp_problem_t p, const double x0[3], dp_trajectory 
     const int N = p->N;
     std::vector<double> h(roll_doubles(N));
     std::vector<int> hu(N, -1);
-    dp_status st = rollout_async(p, x0, h.data(), hu.data(), s);
+    dp_status st = rollout_async(p, x0, h.data(), hu.data(), s, true);
     if (st != DP_OK)
         return st;
     DP_CUDA(cudaStreamSynchronize(s));

@@ -56,7 +56,10 @@ const char *last_error();
 size_t roll_doubles(int N);  // doubles of one rollout record (launch_rollout's layout)
 // Launch the rollout of a solved problem and copy its record to host memory
 // (pinned for an asynchronous copy) on stream s; no synchronisation.
-dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s);
+// overlap: may run beside the last stage of the solve just enqueued on s
+// (only for a caller that synchronizes s before the next rollout)
+dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s,
+                        bool overlap = false);
 // Fill a caller's trajectory from a rollout record; returns its fail stage.
 int unpack_rollout(int N, const double *h, const int *hu, dp_trajectory *traj);
 size_t problem_bytes(const dp_problem *p);  // device bytes the problem holds

@@ -186,6 +186,30 @@ def test_solve_is_deterministic_and_graph_replays(gpu):
         assert torch.equal(v1[k], dp.value(k))
 
 
+def test_rollout_beside_the_last_stage_equals_the_sequential_rollout(gpu):
+    """dp_rollout issued right after the solve, on the solve's stream, starts
+    once J_1 is written, beside the sweep's last Bellman stage (it never reads
+    J_0); after another call on the problem (a profiled sweep, which rewrites
+    every J_k bit for bit), or on another stream, it runs after the whole
+    sweep.  The trajectories are identical."""
+    p = reduced(seed=36)
+    dp = gpu(p)
+    keys = ("v", "soc", "t", "u", "dt", "wait", "fuel")
+    dp.solve()
+    r1 = dp.rollout(raise_infeasible=False)
+    dp.profile_sweep()
+    r2 = dp.rollout(raise_infeasible=False)
+    side = torch.cuda.Stream()
+    dp.solve()
+    torch.cuda.synchronize()
+    r3 = dp.rollout(stream=side, raise_infeasible=False)
+    assert r1["status"] == 0
+    for r in (r2, r3):
+        for key in keys:
+            np.testing.assert_array_equal(r1[key], r[key], err_msg=key)
+        assert (r["fuel_g"], r["time_s"], r["J"]) == (r1["fuel_g"], r1["time_s"], r1["J"])
+
+
 def test_update_matches_fresh_problem(gpu):
     a = reduced(seed=34)
     b = reduced(seed=35)
