@@ -57,7 +57,8 @@ size_t roll_doubles(int N);  // doubles of one rollout record (launch_rollout's 
 // Launch the rollout of a solved problem and copy its record to host memory
 // (pinned for an asynchronous copy) on stream s; no synchronisation.
 // overlap: may run beside the last stage of the solve just enqueued on s
-// (only for a caller that synchronizes s before the next rollout)
+// (only for a caller whose previous rollout of p has completed: the record
+// buffer is rewritten from another stream)
 dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h_u, cudaStream_t s,
                         bool overlap = false);
 // Fill a caller's trajectory from a rollout record; returns its fail stage.

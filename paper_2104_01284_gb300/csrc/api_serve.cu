@@ -204,7 +204,8 @@ dp_status dp_batch_submit(dp_batch_t b, const dp_problem_desc *desc, const doubl
     st = dp_solve_backward(S.p, (void *)S.s);
     if (st != DP_OK)
         return st;
-    st = rollout_async(S.p, x0, S.h_roll, S.h_u, S.s);
+    // beside the sweep's last stage: the slot's previous rollout was collected
+    st = rollout_async(S.p, x0, S.h_roll, S.h_u, S.s, true);
     if (st != DP_OK)
         return st;
     DP_CUDA(cudaEventRecord(S.done, S.s));
