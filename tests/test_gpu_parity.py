@@ -106,12 +106,14 @@ def test_tiled_and_direct_bit_identical(gpu, name):
         a.close()
 
 
-@pytest.mark.parametrize("variant,n_t", [("tiled", 201), ("tiled6", 201), ("tiled", 101), ("tiled", 45)])
+@pytest.mark.parametrize("variant,n_t", [("tiled", 201), ("tiled6", 201), ("tiled", 101), ("tiled", 45),
+                                         ("tiled", 62), ("tiled", 254)])
 def test_unsplit_tiled_sweep_bit_identical(gpu, variant, n_t):
     """A grid with enough tiles for the unsplit tiled kernel (more than half
     of the GPU's resident CTA slots, 4 per SM), whose sweep reads J_{k+1}
     through the corner quads the previous stage wrote (row strides 256, 128
-    and 64 for 201, 101 and 45 time points): every J_k and pi_k of the sweep
+    and 64 for 201, 101 and 45 time points; 62 and 254 fill a stride of 64 and
+    256 exactly, n_t + 2 columns): every J_k and pi_k of the sweep
     equals, bit for bit, the stage hook (plain loads of J_{k+1}) run on the
     sweep's own J_{k+1}, and the direct kernel's sweep.  Two lights cover the
     unpaired window loads of light stages."""
