@@ -203,6 +203,20 @@ dp_status dp_rollout(dp_problem_t p, const double x0[3], dp_trajectory *traj, vo
  * DP_ERR_INTERNAL instead of their result when it is set. */
 dp_status dp_debug_checks(int32_t *enabled, uint64_t *site);
 
+/* FP32 FMA throughput probe (a measurement aid; no counterpart in the
+ * paper).  The Bellman kernels are bound by FP32 issue and their roofline is
+ * quoted against SMs x 128 FP32 lanes x 2 FLOP x SM clock; this call times
+ * `repeats` launches (after one warm-up) of a kernel that keeps every SM's
+ * FP32 pipes busy with independent packed FMAs, on the current device and
+ * stream, and returns the fastest launch's rate.
+ *   repeats: >= 1
+ *   tflops:  (host) FP32 FLOP/s of the fastest launch / 1e12, 2 FLOP per FMA
+ *   ms:      (host) that launch's milliseconds
+ * Allocates a few KB on the stream (cudaMallocAsync) and synchronises it.
+ * DP_ERR_INVALID_ARG for NULL outputs or repeats < 1, DP_ERR_CUDA on a CUDA
+ * failure. */
+dp_status dp_measure_fp32_peak(int32_t repeats, double *tflops, double *ms, void *stream);
+
 /* One stage of the recursion, like dp_solve_stage, for callers that cannot
  * allocate GPU memory.  The paper has no counterpart; this entry point exists
  * for integrations whose memory is fixed after start-up: a controller task

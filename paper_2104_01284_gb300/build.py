@@ -21,7 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libecodp.so")
 CHECKED_LIB = os.path.join(HERE, "libecodp_checked.so")
-SOURCES = ["api.cu", "api_multi.cu", "api_serve.cu", "k_precompute.cu", "k_bellman.cu", "k_rollout.cu", "k_adjoint.cu", "k_batch.cu"]
+SOURCES = ["api.cu", "api_multi.cu", "api_serve.cu", "k_precompute.cu", "k_bellman.cu", "k_rollout.cu", "k_adjoint.cu",
+           "k_batch.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(os.path.dirname(HERE), "include")]

@@ -111,6 +111,10 @@ def check(status: int, where: str):
 # bounds-check report of the checked build (0 / no-op in the production build)
 dp_debug_checks = _sig("dp_debug_checks", C.POINTER(C.c_int32), C.POINTER(C.c_uint64))
 EXPORTED.append("dp_debug_checks")
+# FP32 FMA throughput probe (the measured denominator beside the derived one)
+dp_measure_fp32_peak = _sig("dp_measure_fp32_peak", C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                            C.c_void_p)
+EXPORTED.append("dp_measure_fp32_peak")
 
 
 def debug_checks():
@@ -123,6 +127,15 @@ def debug_checks():
     if st not in (DP_OK, DP_ERR_INTERNAL):
         check(st, "dp_debug_checks")
     return bool(en.value), int(site.value)
+
+
+def measure_fp32_peak(repeats: int = 10, stream=None):
+    """(TFLOP/s, ms) of the fastest of `repeats` launches of the FP32 FMA
+    throughput probe on the current device; synchronises the stream."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    handle = int(stream.cuda_stream) if stream is not None else 0
+    check(dp_measure_fp32_peak(int(repeats), C.byref(tf), C.byref(ms), C.c_void_p(handle)), "dp_measure_fp32_peak")
+    return tf.value, ms.value
 
 
 # allocation-free single stage (static device working memory)

@@ -25,7 +25,7 @@ def native():
 def declared_functions():
     hdr = open(os.path.join(ROOT, "include", "ecodp.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(dp_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(dp_[a-z0-9_]+)\s*\(", hdr)))
 
 
 def test_exports_every_declared_function(native):

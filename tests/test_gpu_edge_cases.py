@@ -85,3 +85,20 @@ def test_edge_case_end_to_end(solver, name):
         assert rg["J"] == pytest.approx(ro["J"], rel=1e-3)
     a.close()
     b.close()
+
+
+def test_fp32_peak_probe_near_the_unit_count_peak():
+    """The library's FP32 FMA throughput probe lands near the unit-count peak
+    the Bellman roofline is quoted against (SMs x 128 lanes x 2 FLOP x SM
+    clock, the clock at most 2.1 GHz), and rejects bad arguments."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes as C
+    from paper_2104_01284_gb300 import native as N
+    tf, ms = N.measure_fp32_peak(5)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    top = sms * 128 * 2 * 2.1e9 / 1e12
+    assert 0.5 * top < tf < 1.05 * top, (tf, top)
+    assert ms > 0
+    x = C.c_double(0.0)
+    assert N.dp_measure_fp32_peak(0, C.byref(x), C.byref(x), None) == N.DP_ERR_INVALID_ARG
