@@ -232,8 +232,9 @@ def run_reference(args):
 def bench_batched(n_inst, dev, stream, steps=2):
     """Batched uneven instances (256 seeded horizons of 20-150 stages, 31-61
     speeds, 31-51 SoC points, 101-251 times, 21x21-31x31 torques x brake,
-    1-6 lights) in one persistent launch under a CUDA graph, with the tile
-    configuration picked by the autotuner on the first 32 instances; against
+    1-6 lights) through the batched API in the mode the autotuner picks on
+    the first 32 instances (one persistent launch under a CUDA graph with its
+    tile configuration, or each instance's graph on internal streams); against
     the same instances solved one at a time by the single-problem path (its
     own CUDA graph per instance, on one stream).  Inputs are far larger than
     L2 (tens of GB), so no flush is needed between steps."""
@@ -247,6 +248,8 @@ def bench_batched(n_inst, dev, stream, steps=2):
             best = tune.autotune(repeats=1, stream=stream)
         bt = EcoDPBatch(probs, device=dev, stream=stream, rows_per_lane=best["rows_per_lane"],
                         ctas_per_sm=best["ctas_per_sm"])
+        if best["streams"]:
+            bt.set_streams(best["streams"])
         bt.solve(stream)
         bt.wait(stream)
         times = []
@@ -262,8 +265,10 @@ def bench_batched(n_inst, dev, stream, steps=2):
         prof = bt.profile(stream)
         info = bt.info()
         bt.close()
-        # the same instances through the single-problem path, one at a time
-        single_ms = 0.0
+        # the same instances through the single-problem path: one at a time,
+        # and spread over 4 streams (the serving loop's way of sharing the GPU)
+        single_ms = streams_ms = 0.0
+        side = [torch.cuda.Stream(device=dev) for _ in range(4)]
         for c0 in range(0, n_inst, 32):
             dps = [EcoDP(q, device=dev, stream=stream) for q in probs[c0:c0 + 32]]
             for d in dps:
@@ -277,6 +282,18 @@ def bench_batched(n_inst, dev, stream, steps=2):
             e1.record(stream)
             e1.synchronize()
             single_ms += e0.elapsed_time(e1)
+            e0.record(stream)
+            for q in side:
+                q.wait_event(e0)
+            for b, d in enumerate(dps):
+                d.solve(side[b % len(side)])
+            for q in side:
+                done = torch.cuda.Event()
+                done.record(q)
+                stream.wait_event(done)
+            e1.record(stream)
+            e1.synchronize()
+            streams_ms += e0.elapsed_time(e1)
             for d in dps:
                 d.close()
     ms = statistics.median(times)
@@ -285,11 +302,13 @@ def bench_batched(n_inst, dev, stream, steps=2):
             "nominal_evals_per_s": info["nominal_evals"] / (ms / 1e3),
             "single_path_solves_per_s": n_inst / (single_ms / 1e3), "single_path_ms": single_ms,
             "speedup_vs_single_path": single_ms / ms,
+            "single_path_4_streams_solves_per_s": n_inst / (streams_ms / 1e3),
             "tile_config": {"rows_per_lane": best["rows_per_lane"], "ctas_per_sm": best["ctas_per_sm"],
-                            "autotune_ms_on_32": best["ms"]},
+                            "streams": best["streams"], "autotune_ms_on_32": best["ms"]},
             "persistent_ms": prof["bellman"], "precompute_ms": prof["precompute"],
             "work_items": info["work_items"], "ctas": info["ctas"], "device_gb": info["device_bytes"] / 1e9,
-            "gpu_launches_per_batch": 3, "steps": steps}
+            "gpu_launches_per_batch": 3 if not best["streams"] else sum(q.n_stages + 3 for q in probs),
+            "steps": steps}
 
 
 def bench_serving(dev, seconds):
@@ -412,7 +431,10 @@ def headline(adjoint, paper_grid, batched, serving):
     if batched:
         h["batched"] = {"instances": batched["instances"], "solves_per_s": batched["solves_per_s"],
                         "single_path_solves_per_s": batched["single_path_solves_per_s"],
-                        "speedup_vs_single_path": batched["speedup_vs_single_path"]}
+                        "speedup_vs_single_path": batched["speedup_vs_single_path"],
+                        "single_path_4_streams_solves_per_s": batched["single_path_4_streams_solves_per_s"],
+                        "mode": (f"{batched['tile_config']['streams']} streams of per-instance graphs"
+                                 if batched["tile_config"]["streams"] else "persistent launch")}
     if serving:
         half = serving["runs"]["half_saturation"]
         one = serving["one_at_a_time"]

@@ -340,17 +340,33 @@ dp_status dp_multi_create(const dp_problem_desc *descs, int32_t n, const dp_mult
 dp_status dp_multi_destroy(dp_multi_t m);
 
 /* Change the tile configuration (rows_per_lane in {0, 4, 8}, ctas_per_sm in
- * [0, the number that fit]); synchronises the creation stream.  Results of
- * earlier solves become stale (DP_ERR_NOT_SOLVED). */
+ * [0, the number that fit]) and select the persistent launch; synchronises
+ * the creation stream.  Results of earlier solves become stale
+ * (DP_ERR_NOT_SOLVED). */
 dp_status dp_multi_set_config(dp_multi_t m, int32_t rows_per_lane, int32_t ctas_per_sm);
 
-/* Solve every instance: terminal values and per-stage tables of all
- * instances (one launch each), then one persistent launch over (instance,
- * stage, tile) work items in wavefront order, each tile of stage k waiting
- * for the tiles of stage k+1 of its instance.  The launches are captured in
- * a CUDA graph on the first call (and after dp_multi_set_config) and replayed
- * on `stream`.  Asynchronous; a dependency wait that gives up (after 10 s) is
- * reported by the next synchronising call as DP_ERR_TIMEOUT. */
+/* Select the per-instance mode (streams in [1, 16]) or return to the
+ * persistent launch (streams = 0).  Per instance: the single-problem sweep
+ * (terminal values, corner quads, tables, one Bellman launch per stage, the
+ * kernels of dp_solve_backward, results bit-identical to it) captured as its
+ * own CUDA graph on the batch's buffers; a solve forks `streams` internal
+ * streams from the caller's stream, deals the instances over them by
+ * decreasing work (each to the stream with the least so far) and joins them
+ * back, so it stays asynchronous on that stream.  The first switch allocates
+ * each instance's two corner-quad slots and captures the graphs (a few ms
+ * per instance); synchronises the creation stream.  Results of earlier
+ * solves become stale. */
+dp_status dp_multi_set_streams(dp_multi_t m, int32_t streams);
+
+/* Solve every instance.  Persistent launch: terminal values and per-stage
+ * tables of all instances (one launch each), then one persistent launch over
+ * (instance, stage, tile) work items in wavefront order, each tile of stage
+ * k waiting for the tiles of stage k+1 of its instance; captured in a CUDA
+ * graph on the first call (and after dp_multi_set_config) and replayed on
+ * `stream`; a dependency wait that gives up (after 10 s) is reported by the
+ * next synchronising call as DP_ERR_TIMEOUT.  Per-instance mode
+ * (dp_multi_set_streams): the instances' graphs on the internal streams,
+ * joined back into `stream`.  Asynchronous either way. */
 dp_status dp_multi_solve(dp_multi_t m, void *stream);
 
 /* Synchronise `stream` and report DP_ERR_TIMEOUT if the last solve's
@@ -359,15 +375,19 @@ dp_status dp_multi_wait(dp_multi_t m, void *stream);
 
 /* One solve with direct launches and CUDA events (same work and results as
  * dp_multi_solve); synchronises and reports ms[0] terminal + precompute
- * launches, ms[1] the persistent Bellman launch, ms[2] the whole solve. */
+ * launches, ms[1] the persistent Bellman launch, ms[2] the whole solve (in
+ * the per-instance mode ms[0] = 0 and ms[1] = ms[2], the instances' graphs
+ * interleaving on the streams). */
 dp_status dp_multi_profile(dp_multi_t m, void *stream, float ms[3]);
 
-/* Autotuner: time every configuration (rows_per_lane in {4, 8} x every
- * ctas_per_sm that fits), `repeats` timed solves each after one warm-up,
- * keep the fastest (minimum whole-solve time) and set it.  best[0] =
- * rows_per_lane, best[1] = ctas_per_sm; *best_ms (may be NULL) its time.
- * Synchronises; leaves the batch solved. */
-dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t best[2], float *best_ms);
+/* Autotuner: time every persistent configuration (rows_per_lane in {4, 8}
+ * x every ctas_per_sm that fits) and the per-instance mode on 2, 4 and 8
+ * streams, `repeats` timed solves each after one warm-up, keep the fastest
+ * (minimum whole-solve time) and set it.  best[0] = rows_per_lane, best[1] =
+ * ctas_per_sm, best[2] = streams (0: the persistent launch won; then best[0]
+ * and best[1] are its configuration, else both 0); *best_ms (may be NULL)
+ * its time.  Synchronises; leaves the batch solved. */
+dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t best[3], float *best_ms);
 
 /* Test hook for the timeout path: raise instance b's per-stage completion
  * target by one, so that every dependency wait on b's stages runs out
@@ -379,8 +399,9 @@ dp_status dp_multi_debug_stall(dp_multi_t m, int32_t b);
 /* out[0] instances, out[1] work items of the persistent launch, out[2] its
  * CTAs, out[3] rows_per_lane, out[4] CTAs per SM, out[5] nominal state x
  * control evaluations of one solve (sum of N n_v n_soc n_t n_controls),
- * out[6] device bytes held, out[7] the longest horizon. */
-dp_status dp_multi_info(dp_multi_t m, int64_t out[8]);
+ * out[6] device bytes held, out[7] the longest horizon, out[8] streams of
+ * the per-instance mode (0: the persistent launch is selected). */
+dp_status dp_multi_info(dp_multi_t m, int64_t out[9]);
 
 /* J_stage / pi_stage of instance b, as dp_get_value / dp_get_policy (dense
  * [n_v][n_soc][n_t] of that instance, device or host memory as flagged).

@@ -53,6 +53,21 @@ struct dp_multi {
     cudaGraphExec_t gexec = nullptr;
     bool solved = false;
 
+    // Per-instance mode (n_streams > 0): each instance's sweep is the
+    // single-problem sequence (terminal values, corner quads, tables, the
+    // Bellman stages) captured as its own CUDA graph on the batch's buffers;
+    // a solve deals the instances over n_streams internal streams forked
+    // from the caller's stream and joins them back.
+    int n_streams = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> ev_done;
+    cudaEvent_t ev_start = nullptr;
+    std::vector<cudaGraphExec_t> inst_graph;  // per instance, captured on first use
+    std::vector<float4 *> quad;               // per instance: two slots, or null
+    std::vector<size_t> quad_elems;
+    std::vector<int> stream_of, launch_order;
+    bool quads_ready = false;
+
     BatchSched sched() const
     {
         return BatchSched{d_order, d_pref, d_start, d_m, max_n, n_items, d_queue, d_error, wait_limit_ns};
@@ -92,11 +107,31 @@ dp_status m_alloc_n(dp_multi *m, size_t n, T **out)
     return s;
 }
 
+void release_streams(dp_multi *m)
+{
+    for (cudaStream_t q : m->streams) {
+        cudaStreamSynchronize(q);
+        cudaStreamDestroy(q);
+    }
+    m->streams.clear();
+    for (cudaEvent_t e : m->ev_done)
+        cudaEventDestroy(e);
+    m->ev_done.clear();
+    if (m->ev_start)
+        cudaEventDestroy(m->ev_start);
+    m->ev_start = nullptr;
+}
+
 void m_release(dp_multi *m)
 {
     if (m->gexec)
         cudaGraphExecDestroy(m->gexec);
     m->gexec = nullptr;
+    for (cudaGraphExec_t g : m->inst_graph)
+        if (g)
+            cudaGraphExecDestroy(g);
+    m->inst_graph.clear();
+    release_streams(m);
     if (m->cap_stream)
         cudaStreamDestroy(m->cap_stream);
     m->cap_stream = nullptr;
@@ -172,6 +207,119 @@ dp_status check_error_flag(dp_multi *m, cudaStream_t s)
     return DP_OK;
 }
 
+// One instance's sweep with the single-problem launchers on the batch's
+// buffers (results identical to a dp_problem of the same descriptor).
+dp_status enqueue_instance(dp_multi *m, int b, cudaStream_t s)
+{
+    const DevParams &P = m->hP[b];
+    const BatchInst &I = m->h_inst[b];
+    const DevParams *dP = m->d_params + b;
+    float4 *q = m->quad[b];
+    auto V = [&](int k) { return I.V + (size_t)k * I.stage_elems; };
+    auto Q = [&](int k) { return q ? q + (size_t)(k & 1) * m->quad_elems[b] : nullptr; };
+    DP_CUDA(launch_terminal(dP, P, V(P.N), s));
+    if (q)
+        DP_CUDA(launch_quad_from_pad(P, V(P.N), Q(P.N), s));
+    DP_CUDA(launch_precompute(dP, P, I.tb, 0, P.N, I.sc, s));
+    for (int k = P.N - 1; k >= 0; --k)
+        DP_CUDA(launch_bellman(dP, P, I.tb, k, I.sc, V(k + 1), V(k), I.pi + (size_t)k * I.pi_elems, 1, s, Q(k + 1),
+                               Q(k)));
+    return DP_OK;
+}
+
+// Switch to the per-instance mode with K streams: corner quads and per-instance
+// graphs on first use, the instances dealt by decreasing work to the stream
+// with the least work so far.
+dp_status set_streams(dp_multi *m, int K)
+{
+    if (K < 1 || K > 16)
+        return fail(DP_ERR_INVALID_ARG, "streams must be in [1, 16]");
+    cudaStream_t cs = m->create_stream;
+    if (!m->quads_ready) {
+        m->quad.assign(m->B, nullptr);
+        m->quad_elems.assign(m->B, 0);
+        for (int b = 0; b < m->B; ++b) {
+            const DevParams &P = m->hP[b];
+            const size_t e = (size_t)P.n_v * quad_rows(P.n_xi) * quad_ld(P.n_t);
+            if (e == 0)
+                continue;
+            dp_status st = m_alloc_n(m, 2 * e, &m->quad[b]);
+            if (st != DP_OK)
+                return st;
+            m->quad_elems[b] = e;
+            DP_CUDA(launch_fill(reinterpret_cast<float *>(m->quad[b]), 8 * e, V_BIG, cs));
+        }
+        DP_CUDA(cudaStreamSynchronize(cs));
+        m->quads_ready = true;
+    }
+    if (m->inst_graph.empty()) {
+        m->inst_graph.assign(m->B, nullptr);
+        for (int b = 0; b < m->B; ++b) {
+            cudaGraph_t g = nullptr;
+            DP_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+            dp_status st = enqueue_instance(m, b, m->cap_stream);
+            cudaError_t e = cudaStreamEndCapture(m->cap_stream, &g);
+            if (st != DP_OK) {
+                if (g)
+                    cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess)
+                return fail(DP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&m->inst_graph[b], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                m->inst_graph[b] = nullptr;
+                return fail(DP_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            }
+        }
+    }
+    if ((int)m->streams.size() != K) {
+        release_streams(m);
+        m->streams.assign(K, nullptr);
+        m->ev_done.assign(K, nullptr);
+        for (int q = 0; q < K; ++q) {
+            DP_CUDA(cudaStreamCreateWithFlags(&m->streams[q], cudaStreamNonBlocking));
+            DP_CUDA(cudaEventCreateWithFlags(&m->ev_done[q], cudaEventDisableTiming));
+        }
+        DP_CUDA(cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming));
+    }
+    std::vector<double> work(m->B);
+    for (int b = 0; b < m->B; ++b) {
+        const DevParams &P = m->hP[b];
+        work[b] = (double)P.N * P.n_v * P.n_xi * P.n_t * P.n_u;
+    }
+    m->launch_order.resize(m->B);
+    std::iota(m->launch_order.begin(), m->launch_order.end(), 0);
+    std::stable_sort(m->launch_order.begin(), m->launch_order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> load(K, 0.0);
+    m->stream_of.assign(m->B, 0);
+    for (int b : m->launch_order) {
+        const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        m->stream_of[b] = q;
+        load[q] += work[b];
+    }
+    m->n_streams = K;
+    m->solved = false;
+    return DP_OK;
+}
+
+// The per-instance solve on the caller's stream s (forked and joined).
+dp_status enqueue_streams(dp_multi *m, cudaStream_t s)
+{
+    DP_CUDA(cudaMemsetAsync(m->d_error, 0, sizeof(int), s));  // no dependency waits in this mode
+    DP_CUDA(cudaEventRecord(m->ev_start, s));
+    for (cudaStream_t q : m->streams)
+        DP_CUDA(cudaStreamWaitEvent(q, m->ev_start, 0));
+    for (int b : m->launch_order)
+        DP_CUDA(cudaGraphLaunch(m->inst_graph[b], m->streams[m->stream_of[b]]));
+    for (size_t q = 0; q < m->streams.size(); ++q) {
+        DP_CUDA(cudaEventRecord(m->ev_done[q], m->streams[q]));
+        DP_CUDA(cudaStreamWaitEvent(s, m->ev_done[q], 0));
+    }
+    return DP_OK;
+}
+
 dp_status set_config(dp_multi *m, int rows_per_lane, int ctas_per_sm)
 {
     if (rows_per_lane != 0 && rows_per_lane != 4 && rows_per_lane != 8)
@@ -184,6 +332,7 @@ dp_status set_config(dp_multi *m, int rows_per_lane, int ctas_per_sm)
         return fail(DP_ERR_INVALID_ARG, "ctas_per_sm must be in [0, " + std::to_string(fit) + "]");
     m->rows_per_lane = R;
     m->ctas_per_sm = ctas_per_sm;
+    m->n_streams = 0;
     if (m->gexec)
         cudaGraphExecDestroy(m->gexec);
     m->gexec = nullptr;
@@ -317,6 +466,7 @@ dp_status dp_multi_create(const dp_problem_desc *descs, int32_t n, const dp_mult
             return fail(DP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
         return DP_OK;
     };
+    TRY(cuda_try(cudaMemsetAsync(m->d_error, 0, sizeof(int), s), "clear error flag"));
     TRY(cuda_try(cudaMemcpyAsync(m->d_params, m->hP.data(), n * sizeof(DevParams), cudaMemcpyHostToDevice, s),
                  "copy params"));
     TRY(cuda_try(cudaMemcpyAsync(m->d_grade, all_grade.data(), all_grade.size() * sizeof(float),
@@ -376,6 +526,13 @@ dp_status dp_multi_solve(dp_multi_t m, void *stream)
     if (!m)
         return fail(DP_ERR_INVALID_ARG, "batch is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->n_streams > 0) {
+        dp_status st = enqueue_streams(m, s);
+        if (st != DP_OK)
+            return st;
+        m->solved = true;
+        return DP_OK;
+    }
     if (!m->gexec) {
         cudaGraph_t g = nullptr;
         DP_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -417,7 +574,13 @@ dp_status dp_multi_profile(dp_multi_t m, void *stream, float ms[3])
         DP_CUDA(cudaEventCreate(&e));
     auto run = [&]() -> dp_status {
         DP_CUDA(cudaEventRecord(ev[0], s));
-        dp_status st = enqueue_multi(m, s, ev[1]);
+        dp_status st = DP_OK;
+        if (m->n_streams > 0) {  // not separable: everything counts as Bellman time
+            DP_CUDA(cudaEventRecord(ev[1], s));
+            st = enqueue_streams(m, s);
+        } else {
+            st = enqueue_multi(m, s, ev[1]);
+        }
         if (st != DP_OK)
             return st;
         DP_CUDA(cudaEventRecord(ev[2], s));
@@ -435,14 +598,23 @@ dp_status dp_multi_profile(dp_multi_t m, void *stream, float ms[3])
     return st;
 }
 
-dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t best[2], float *best_ms)
+dp_status dp_multi_set_streams(dp_multi_t m, int32_t streams)
+{
+    if (!m)
+        return fail(DP_ERR_INVALID_ARG, "batch is NULL");
+    if (streams == 0)
+        return set_config(m, m->rows_per_lane, m->ctas_per_sm);
+    return set_streams(m, streams);
+}
+
+dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t best[3], float *best_ms)
 {
     if (!m || !best)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (repeats < 1 || repeats > 100)
         return fail(DP_ERR_INVALID_ARG, "repeats must be in [1, 100]");
     float t_best = INFINITY;
-    int r_best = 0, c_best = 0;
+    int r_best = 0, c_best = 0, k_best = 0;
     const int Rs[2] = {4, 8};
     for (int R : Rs) {
         const int fit = persistent_max_ctas_per_sm(R, m->max_n_cls, m->max_n_u);
@@ -466,15 +638,36 @@ dp_status dp_multi_autotune(dp_multi_t m, void *stream, int32_t repeats, int32_t
             }
         }
     }
-    dp_status st = set_config(m, r_best, c_best);
+    // the per-instance mode on 2, 4 and 8 streams
+    const int Ks[3] = {2, 4, 8};
+    for (int K : Ks) {
+        dp_status st = set_streams(m, K);
+        if (st != DP_OK)
+            return st;
+        float t = INFINITY;
+        for (int q = 0; q < repeats + 1; ++q) {
+            float ms[3];
+            st = dp_multi_profile(m, stream, ms);
+            if (st != DP_OK)
+                return st;
+            if (q > 0)
+                t = std::min(t, ms[2]);
+        }
+        if (t < t_best) {
+            t_best = t;
+            k_best = K;
+        }
+    }
+    dp_status st = k_best > 0 ? set_streams(m, k_best) : set_config(m, r_best, c_best);
     if (st != DP_OK)
         return st;
     float ms[3];
     st = dp_multi_profile(m, stream, ms);  // leaves the batch solved in the chosen configuration
     if (st != DP_OK)
         return st;
-    best[0] = r_best;
-    best[1] = c_best;
+    best[0] = k_best > 0 ? 0 : r_best;
+    best[1] = k_best > 0 ? 0 : c_best;
+    best[2] = k_best;
     if (best_ms)
         *best_ms = t_best;
     return DP_OK;
@@ -491,7 +684,7 @@ dp_status dp_multi_debug_stall(dp_multi_t m, int32_t b)
     return DP_OK;
 }
 
-dp_status dp_multi_info(dp_multi_t m, int64_t out[8])
+dp_status dp_multi_info(dp_multi_t m, int64_t out[9])
 {
     if (!m || !out)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
@@ -511,6 +704,7 @@ dp_status dp_multi_info(dp_multi_t m, int64_t out[8])
     out[5] = nominal;
     out[6] = (int64_t)m->bytes_held;
     out[7] = m->max_n;
+    out[8] = m->n_streams;
     return DP_OK;
 }
 

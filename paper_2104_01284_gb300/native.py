@@ -157,6 +157,7 @@ dp_multi_create = _sig("dp_multi_create", C.POINTER(ProblemDesc), C.c_int32, C.P
                        C.POINTER(Allocator), vp, C.POINTER(vp))
 dp_multi_destroy = _sig("dp_multi_destroy", vp)
 dp_multi_set_config = _sig("dp_multi_set_config", vp, C.c_int32, C.c_int32)
+dp_multi_set_streams = _sig("dp_multi_set_streams", vp, C.c_int32)
 dp_multi_solve = _sig("dp_multi_solve", vp, vp)
 dp_multi_wait = _sig("dp_multi_wait", vp, vp)
 dp_multi_profile = _sig("dp_multi_profile", vp, vp, C.POINTER(C.c_float))
@@ -168,7 +169,7 @@ dp_multi_get_policy = _sig("dp_multi_get_policy", vp, C.c_int32, C.c_int32, vp, 
 dp_multi_rollout = _sig("dp_multi_rollout", vp, dbl_p, C.POINTER(Trajectory), vp)
 EXPORTED += ["dp_multi_create", "dp_multi_destroy", "dp_multi_set_config", "dp_multi_solve", "dp_multi_wait",
              "dp_multi_profile", "dp_multi_autotune", "dp_multi_info", "dp_multi_get_value", "dp_multi_get_policy",
-             "dp_multi_rollout", "dp_multi_debug_stall"]
+             "dp_multi_rollout", "dp_multi_debug_stall", "dp_multi_set_streams"]
 
 # serving: continuous batching of receding-horizon re-solves
 dp_batch_create = _sig("dp_batch_create", C.c_int32, C.c_size_t, C.POINTER(Allocator), C.POINTER(vp))

@@ -328,8 +328,15 @@ class EcoDPBatch:
         return len(self.probs)
 
     def set_config(self, rows_per_lane: int, ctas_per_sm: int):
+        """The persistent launch with this tile configuration."""
         with torch.cuda.device(self.device):
             N.check(N.dp_multi_set_config(self.h, int(rows_per_lane), int(ctas_per_sm)), "dp_multi_set_config")
+
+    def set_streams(self, streams: int):
+        """The per-instance mode on `streams` internal streams (0: back to the
+        persistent launch)."""
+        with torch.cuda.device(self.device):
+            N.check(N.dp_multi_set_streams(self.h, int(streams)), "dp_multi_set_streams")
 
     def solve(self, stream=None):
         with torch.cuda.device(self.device):
@@ -346,12 +353,12 @@ class EcoDPBatch:
         return dict(precompute=ms[0], bellman=ms[1], solve=ms[2])
 
     def autotune(self, repeats: int = 1, stream=None):
-        best = (C.c_int32 * 2)()
+        best = (C.c_int32 * 3)()
         t = C.c_float(0.0)
         with torch.cuda.device(self.device):
             N.check(N.dp_multi_autotune(self.h, _stream_handle(stream), int(repeats), best, C.byref(t)),
                     "dp_multi_autotune")
-        return dict(rows_per_lane=best[0], ctas_per_sm=best[1], ms=t.value)
+        return dict(rows_per_lane=best[0], ctas_per_sm=best[1], streams=best[2], ms=t.value)
 
     def debug_stall(self, b: int):
         """Test hook: make every dependency wait on instance b run out."""
@@ -359,11 +366,11 @@ class EcoDPBatch:
             N.check(N.dp_multi_debug_stall(self.h, int(b)), "dp_multi_debug_stall")
 
     def info(self):
-        out = (C.c_int64 * 8)()
+        out = (C.c_int64 * 9)()
         with torch.cuda.device(self.device):
             N.check(N.dp_multi_info(self.h, out), "dp_multi_info")
         keys = ("instances", "work_items", "ctas", "rows_per_lane", "ctas_per_sm", "nominal_evals", "device_bytes",
-                "max_horizon")
+                "max_horizon", "streams")
         return dict(zip(keys, list(out)))
 
     def _shape(self, b):

@@ -77,6 +77,41 @@ def test_batch_bit_identical_to_alone(mods, small, R, c):
             same_traj(rb, alone[b][2])
 
 
+@pytest.mark.parametrize("streams", [1, 3])
+def test_batch_per_instance_streams_bit_identical_to_alone(mods, small, streams):
+    """The per-instance mode (each instance's single-problem sweep as its own
+    graph, the instances dealt over internal streams) equals single solves bit
+    for bit, rollouts included; switching back selects the persistent launch,
+    whose results are the same."""
+    probs, alone = small
+    with mods.EcoDPBatch(probs) as bt:
+        bt.set_streams(streams)
+        assert bt.info()["streams"] == streams
+        bt.solve()
+        bt.wait()
+        for b, p in enumerate(probs):
+            V, pi, ro = alone[b]
+            for k in range(p.n_stages + 1):
+                assert np.array_equal(bits(bt.value(b, k).cpu().numpy()), bits(V[k])), f"inst {b} V{k}"
+            for k in range(p.n_stages):
+                assert np.array_equal(bt.policy(b, k).cpu().numpy(), pi[k]), f"inst {b} pi{k}"
+        for b, rb in enumerate(bt.rollout(raise_infeasible=False)):
+            same_traj(rb, alone[b][2])
+        bt.solve()  # a second solve through the same graphs
+        bt.wait()
+        assert np.array_equal(bits(bt.value(0, 0).cpu().numpy()), bits(alone[0][0][0]))
+        bt.set_streams(0)
+        assert bt.info()["streams"] == 0
+        bt.solve()
+        bt.wait()
+        for b in range(len(probs)):
+            assert np.array_equal(bits(bt.value(b, 0).cpu().numpy()), bits(alone[b][0][0]))
+        import paper_2104_01284_gb300.native as N
+        with pytest.raises(N.DPError) as e:
+            bt.set_streams(17)
+        assert e.value.status == N.DP_ERR_INVALID_ARG
+
+
 def test_batch_end_to_end_oracle_parity(mods):
     probs = P.config3_small(seed=34, n_instances=4)
     with mods.EcoDPBatch(probs) as bt:
@@ -107,7 +142,8 @@ def test_batch_repeat_and_reconfigure(mods, small):
             bt.value(0, 0)
         assert e.value.status == N.DP_ERR_NOT_SOLVED
         best = bt.autotune(repeats=1)
-        assert best["rows_per_lane"] in (4, 8) and best["ctas_per_sm"] >= 1
+        assert best["streams"] in (2, 4, 8) or (best["rows_per_lane"] in (4, 8) and best["ctas_per_sm"] >= 1)
+        assert bt.info()["streams"] == best["streams"]
         for b in range(len(probs)):
             assert torch.equal(first[b], bt.value(b, 0))
 
