@@ -464,7 +464,8 @@ def run_ours(args):
     p = workload(args.seed)
     stream = torch.cuda.Stream(dev)
     dp = EcoDP(p, device=dev, stream=stream)
-    launches_per_step = 1 + 1 + p.n_stages + 1  # terminal, precompute (all stages), N x Bellman, rollout
+    # terminal, J_N's corner quads, precompute (all stages), N x Bellman, rollout
+    launches_per_step = 1 + 1 + 1 + p.n_stages + 1
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
