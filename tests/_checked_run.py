@@ -96,6 +96,11 @@ def main():
         bt.wait()
         bt.rollout(raise_infeasible=False)
         clean("batch", done)
+        bt.set_streams(2)  # the per-instance mode: single-problem graphs on 2 streams
+        bt.solve()
+        bt.wait()
+        bt.rollout(raise_infeasible=False)
+        clean("batch_streams", done)
     print(json.dumps({"phases": done, "digest": digest, "hashes": hashes}))
 
 
