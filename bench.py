@@ -420,7 +420,7 @@ def bench_paper_grid(dev, stream, reps=20):
 
 
 ROOFLINE_KEYS = ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic", "peak_basis",
-                 "peak_measured", "frac_of_measured", "bellman_ms_per_launch", "share_of_sweep")
+                 "peak_measured", "frac_of_measured", "onchip_peaks_gbs", "bellman_ms_per_launch", "share_of_sweep")
 
 
 def headline(adjoint, paper_grid, batched, serving):
@@ -543,6 +543,9 @@ def run_ours(args):
     meas_tf, _ = N.measure_fp32_peak(10, stream)
     roofline["peak_measured"] = meas_tf
     roofline["frac_of_measured"] = achieved / meas_tf if meas_tf > 0 else None
+    # the on-chip load paths' measured rates (shared memory, L1 hits, L2
+    # hits), the kernel's other possible bounds
+    roofline["onchip_peaks_gbs"] = {k: N.measure_onchip_bw(k, 5, stream)[0] for k in ("smem", "l1", "l2")}
 
     # end to end through the public API with host buffers: upload the
     # problem tables, solve, read the trajectory back, every step

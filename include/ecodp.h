@@ -217,6 +217,22 @@ dp_status dp_debug_checks(int32_t *enabled, uint64_t *site);
  * failure. */
 dp_status dp_measure_fp32_peak(int32_t repeats, double *tflops, double *ms, void *stream);
 
+/* On-chip load bandwidth probes, the measured peaks beside the Bellman
+ * kernel's rates (a measurement aid; the paper has no counterpart).  Every
+ * thread of SMs x 6 CTAs of 256 threads keeps 8 independent 16-byte loads in
+ * flight:
+ *   kind 0: shared memory (32 KB per CTA, conflict-free);
+ *   kind 1: L1 (each CTA re-reads its own 16 KB of a global buffer with
+ *           ld.global.ca; after the first pass every load hits);
+ *   kind 2: L2 (a 64 MB buffer, inside the L2, streamed with L2-only loads).
+ * Each kind runs one warm-up launch and `repeats` timed launches on stream
+ * and reports the fastest: *gbs = bytes loaded / time in GB/s (1e9 B/s),
+ * *ms = that launch's time.  Allocates and frees (stream-ordered) at most
+ * 64 MB; synchronises stream.  DP_ERR_INVALID_ARG for a null output,
+ * repeats < 1 or another kind.
+ */
+dp_status dp_measure_onchip_bw(int32_t kind, int32_t repeats, double *gbs, double *ms, void *stream);
+
 /* One stage of the recursion, like dp_solve_stage, for callers that cannot
  * allocate GPU memory.  The paper has no counterpart; this entry point exists
  * for integrations whose memory is fixed after start-up: a controller task

@@ -115,6 +115,11 @@ EXPORTED.append("dp_debug_checks")
 dp_measure_fp32_peak = _sig("dp_measure_fp32_peak", C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.c_void_p)
 EXPORTED.append("dp_measure_fp32_peak")
+# on-chip load bandwidth probes (shared memory, L1, L2)
+dp_measure_onchip_bw = _sig("dp_measure_onchip_bw", C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), C.c_void_p)
+EXPORTED.append("dp_measure_onchip_bw")
+ONCHIP_KINDS = {"smem": 0, "l1": 1, "l2": 2}
 
 
 def debug_checks():
@@ -136,6 +141,17 @@ def measure_fp32_peak(repeats: int = 10, stream=None):
     handle = int(stream.cuda_stream) if stream is not None else 0
     check(dp_measure_fp32_peak(int(repeats), C.byref(tf), C.byref(ms), C.c_void_p(handle)), "dp_measure_fp32_peak")
     return tf.value, ms.value
+
+
+def measure_onchip_bw(kind: str, repeats: int = 10, stream=None):
+    """(GB/s, ms) of the fastest of `repeats` launches of the load bandwidth
+    probe `kind` ("smem", "l1" or "l2") on the current device; synchronises
+    the stream."""
+    gbs, ms = C.c_double(0.0), C.c_double(0.0)
+    handle = int(stream.cuda_stream) if stream is not None else 0
+    check(dp_measure_onchip_bw(ONCHIP_KINDS[kind], int(repeats), C.byref(gbs), C.byref(ms), C.c_void_p(handle)),
+          "dp_measure_onchip_bw")
+    return gbs.value, ms.value
 
 
 # allocation-free single stage (static device working memory)

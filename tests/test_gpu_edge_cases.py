@@ -102,3 +102,24 @@ def test_fp32_peak_probe_near_the_unit_count_peak():
     assert ms > 0
     x = C.c_double(0.0)
     assert N.dp_measure_fp32_peak(0, C.byref(x), C.byref(x), None) == N.DP_ERR_INVALID_ARG
+
+
+def test_onchip_bandwidth_probes_within_the_load_path_limits():
+    """The shared-memory, L1 and L2 load bandwidth probes report rates below
+    the load path's limit (128 bytes per SM per clock, the clock at most
+    2.1 GHz) and well above the HBM copy rate (a probe whose loads missed
+    their level would fall to HBM speed); L2 is the slowest of the three.
+    Bad arguments are rejected."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes as C
+    from paper_2104_01284_gb300 import native as N
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    top = sms * 128 * 2.1e9 / 1e9  # GB/s
+    r = {k: N.measure_onchip_bw(k, 3)[0] for k in ("smem", "l1", "l2")}
+    assert 0.3 * top < r["smem"] < 1.05 * top, (r, top)
+    assert 0.2 * top < r["l1"] < 1.05 * top, (r, top)
+    assert 9000.0 < r["l2"] < min(r["smem"], r["l1"]), r
+    x = C.c_double(0.0)
+    assert N.dp_measure_onchip_bw(3, 1, C.byref(x), C.byref(x), None) == N.DP_ERR_INVALID_ARG
+    assert N.dp_measure_onchip_bw(0, 0, C.byref(x), C.byref(x), None) == N.DP_ERR_INVALID_ARG
