@@ -150,7 +150,19 @@ def cpu_baseline(p, target_s, seed=11, single_s=4.0):
     n, dt = timed(target_s, cores)
     n1, dt1 = timed(single_s, 1)
     evals, evals1 = n * p.n_controls, n1 * p.n_controls
+    # the tiny configuration (10 stages, 11 x 11 x 21 states, 11 x 11
+    # torques) solved whole, the same solve the GPU times in bench_c0
+    p0 = P.config0()
+    op0 = O.make(p0)
+    c0 = {}
+    for key, nthreads in (("all_cores", 0), ("one_core", 1)):
+        O.solve(op0, nthreads=nthreads)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            O.solve(op0, nthreads=nthreads)
+        c0[key + "_ms_per_solve"] = 1e3 * (time.perf_counter() - t0) / 3
     return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "c0_full_solve": dict(c0, evals_per_solve=p0.evals_per_solve, cores=cores),
             "sample": f"one Bellman stage (k={k}) of the bench instance at {n} random states x "
                       f"{p.n_controls} controls = {evals:.3e} evals in {dt:.1f} s, FP64, OpenMP",
             "single_core": {"value": evals1 / dt1, "unit": UNIT, "cores": 1,
@@ -389,6 +401,36 @@ def bench_fleet_persistent(dev, stream, n_req=16, steps=3):
             "tile_config": {"rows_per_lane": best["rows_per_lane"], "ctas_per_sm": best["ctas_per_sm"]}}
 
 
+def bench_c0(dev, stream, reps=20):
+    """The tiny configuration (10 stages, 11 x 11 x 21 states, 11 x 11
+    torques, one light = 3.1e6 nominal evaluations per solve): median and
+    p99 of `reps` graph-launched solves, each followed by its rollout."""
+    import torch
+
+    from paper_2104_01284_gb300 import problems as P
+    from paper_2104_01284_gb300.solver import EcoDP
+    p = P.config0()
+    dp = EcoDP(p, device=dev, stream=stream)
+    for _ in range(3):
+        dp.solve(stream)
+        dp.rollout(stream=stream, raise_infeasible=False)
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dp.solve(stream)
+        dp.rollout(stream=stream, raise_infeasible=False)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    dp.close()
+    ms = statistics.median(times)
+    return {"workload": "tiny configuration: 10 stages x 11x11x21 states x 11x11 torques, one light (seed 0)",
+            "evals_per_solve": p.evals_per_solve, "ms_per_solve_median": ms,
+            "ms_per_solve_p99": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))]}
+
+
 def bench_paper_grid(dev, stream, reps=20):
     """The grid of the paper's Table I (20 steps, 35 x 26 x 40 states, 23 x 30
     torques = 5.0e8 nominal evaluations per solve), solved by the
@@ -423,11 +465,13 @@ ROOFLINE_KEYS = ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic
                  "peak_measured", "frac_of_measured", "onchip_peaks_gbs", "bellman_ms_per_launch", "share_of_sweep")
 
 
-def headline(adjoint, paper_grid, batched, serving):
-    """Compact numbers of the adjoint, the paper's Table I grid, the
-    256-instance batch and the serving loop."""
+def headline(adjoint, paper_grid, batched, serving, c0=None):
+    """Compact numbers of the adjoint, the paper's Table I grid, the tiny
+    configuration, the 256-instance batch and the serving loop."""
     h = {"adjoint_ms_per_call": adjoint["ms_per_call"],
          "paper_grid_ms_per_solve": paper_grid["ms_per_solve_median"]}
+    if c0:
+        h["c0_ms_per_solve_and_rollout"] = c0["ms_per_solve_median"]
     if batched:
         h["batched"] = {"instances": batched["instances"], "solves_per_s": batched["solves_per_s"],
                         "single_path_solves_per_s": batched["single_path_solves_per_s"],
@@ -575,6 +619,7 @@ def run_ours(args):
                "dJ_dtheta": dict(zip(("mass", "cda", "crr", "r0", "fuel_scale"), map(float, grad)))}
 
     paper_grid = bench_paper_grid(dev, stream)
+    c0 = bench_c0(dev, stream)
     batched = bench_batched(args.batch, dev, stream) if args.batch > 0 else None
     serving = bench_serving(dev, args.serve_seconds) if args.serve_seconds > 0 else None
 
@@ -594,9 +639,9 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     # the other workloads' headline numbers on the JSON line; their full
     # records (per offered load, tile configuration, ...) go to stderr first
-    line["headline"] = headline(adjoint, paper_grid, batched, serving)
+    line["headline"] = headline(adjoint, paper_grid, batched, serving, c0)
     if rank == 0:
-        print(json.dumps({"details": {"adjoint": adjoint, "paper_grid": paper_grid, "batched": batched,
+        print(json.dumps({"details": {"adjoint": adjoint, "paper_grid": paper_grid, "c0": c0, "batched": batched,
                                       "serving": serving, "roofline": roofline}}), file=sys.stderr, flush=True)
         line["roofline"] = {k: v for k, v in roofline.items() if k in ROOFLINE_KEYS}
         print(json.dumps(line), flush=True)
