@@ -155,7 +155,7 @@ def cpu_baseline(p, target_s, seed=11, single_s=4.0):
     p0 = P.config0()
     op0 = O.make(p0)
     c0 = {}
-    for key, nthreads in (("all_cores", 0), ("one_core", 1)):
+    for key, nthreads in (("all_cores", cores), ("one_core", 1)):
         O.solve(op0, nthreads=nthreads)
         t0 = time.perf_counter()
         for _ in range(3):
