@@ -139,32 +139,59 @@ __device__ __forceinline__ int class_of(const DevParams &P, int ie, int im, int 
     return b * (P.n_cls / P.n_b) + (P.class_sum ? (ie + im) : (ie * P.n_tm + im));
 }
 
-// Block-wide exclusive scan of one int per thread; returns the prefix and
-// writes the block total.  buf holds blockDim.x ints.
-__device__ int block_exclusive_scan(int x, int *buf, int &total)
+// Block-wide exclusive scan of three ints per thread (warp shuffles, then
+// the warps' totals through buf, which holds 3 ints per warp); returns the
+// prefixes and writes the block totals.  Every thread of the block calls it.
+__device__ int3 block_exclusive_scan3(int3 x, int *buf, int3 &total)
 {
-    int tid = threadIdx.x;
-    buf[tid] = x;
-    __syncthreads();
-    for (int off = 1; off < blockDim.x; off <<= 1) {
-        int y = tid >= off ? buf[tid - off] : 0;
-        __syncthreads();
-        buf[tid] += y;
-        __syncthreads();
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = (blockDim.x + 31) >> 5;
+    int3 inc = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int a = __shfl_up_sync(full, inc.x, off), b = __shfl_up_sync(full, inc.y, off),
+                  c = __shfl_up_sync(full, inc.z, off);
+        if (lane >= off) {
+            inc.x += a;
+            inc.y += b;
+            inc.z += c;
+        }
     }
-    int incl = buf[tid];
-    total = buf[blockDim.x - 1];
+    if (lane == 31) {
+        buf[3 * warp] = inc.x;
+        buf[3 * warp + 1] = inc.y;
+        buf[3 * warp + 2] = inc.z;
+    }
     __syncthreads();
-    return incl - x;
+    int3 base = make_int3(0, 0, 0);
+    total = make_int3(0, 0, 0);
+    for (int w = 0; w < n_warps; ++w) {
+        const int3 t = make_int3(buf[3 * w], buf[3 * w + 1], buf[3 * w + 2]);
+        if (w < warp) {
+            base.x += t.x;
+            base.y += t.y;
+            base.z += t.z;
+        }
+        total.x += t.x;
+        total.y += t.y;
+        total.z += t.z;
+    }
+    __syncthreads();  // buf is reused by the next call
+    return make_int3(base.x + inc.x - x.x, base.y + inc.y - x.y, base.z + inc.z - x.z);
 }
 
-// shared per-control result
+// Shared per-control result.  next and below link the members of one (class,
+// shift bucket) into the sorted order and the envelope stack of
+// bucket_envelope (-1 ends a list): each control belongs to one bucket, and
+// one thread builds that bucket's lists.
 struct CtrlRec {
     float cost, f;
-    int d, ok;  // ok: 1 feasible, 2 feasible and on its bucket's lower envelope
+    short d;     // SoC shift, clamped to the 16-bit range (any |d| > 2 is a rare "other" shift)
+    short ok;    // 1 feasible, 2 feasible and on its bucket's lower envelope
+    short next;  // sorted order
+    short below; // envelope stack
 };
-
-constexpr int MAX_MEMBERS = 128;  // controls of one torque class (<= min(n_te, n_tm) <= 90)
+static_assert(sizeof(CtrlRec) == 16, "16-byte per-control records");
 
 // Lower envelope of the lines y_u(x) = cost_u + f_u x over all real x, for
 // the feasible members of class c with SoC shift d (bucket d + 2): marks the
@@ -176,55 +203,77 @@ constexpr int MAX_MEMBERS = 128;  // controls of one torque class (<= min(n_te, 
 // lower cost, then lower u, first); a line between two others is dropped only
 // when it lies on or above their lower envelope everywhere by a clear margin,
 // so FP32 rounding never drops a line that is lowest over a real interval.
+// (f desc, cost asc, u asc): o (control ou) comes before r (control u)
+__device__ __forceinline__ bool line_before(const CtrlRec &o, int ou, const CtrlRec &r, int u)
+{
+    return o.f > r.f || (o.f == r.f && (o.cost < r.cost || (o.cost == r.cost && ou < u)));
+}
+
 __device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, int d, CtrlRec *s_ctrl)
 {
-    short ord[MAX_MEMBERS];
-    int m = 0;
-    // insertion by (f desc, cost asc, u asc).  Members arrive in decreasing
-    // engine torque: within a class and shift bucket the SoC fraction f falls
-    // with the motor share, so most arrive already in order (O(1) each)
-    for (int ie = mem.ie_hi; ie >= mem.ie_lo && m < MAX_MEMBERS; --ie) {
+    // the bucket's members sorted by (f desc, cost asc, u asc), linked
+    // through next.  Members arrive in decreasing engine torque: within a
+    // class and shift bucket the SoC fraction f falls with the motor share,
+    // so most append at the tail (O(1) each); the others walk from the head.
+    int head = -1, tail = -1, m = 0;
+    for (int ie = mem.ie_hi; ie >= mem.ie_lo; --ie) {
         const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
         if (!DP_IN(u, P.n_u))
             continue;
         const CtrlRec r = s_ctrl[u];
         if (!r.ok || r.d != d)
             continue;
-        int q = m++;
-        while (q > 0) {
-            const int ou = ord[q - 1];
-            const CtrlRec o = s_ctrl[ou];
-            if (o.f > r.f || (o.f == r.f && (o.cost < r.cost || (o.cost == r.cost && ou < u))))
-                break;
-            ord[q] = ord[q - 1];
-            --q;
+        ++m;
+        if (tail < 0 || line_before(s_ctrl[tail], tail, r, u)) {
+            s_ctrl[u].next = -1;
+            if (tail < 0)
+                head = u;
+            else
+                s_ctrl[tail].next = (short)u;
+            tail = u;
+            continue;
         }
-        ord[q] = (short)u;
+        int prev = -1, cur = head;
+        for (int g = 0; g < m && DP_IN(cur, P.n_u) && line_before(s_ctrl[cur], cur, r, u); ++g) {
+            prev = cur;
+            cur = s_ctrl[cur].next;
+        }
+        s_ctrl[u].next = (short)cur;
+        if (prev < 0)
+            head = u;
+        else
+            s_ctrl[prev].next = (short)u;
     }
-    short stk[MAX_MEMBERS];
-    int n = 0;
-    for (int q = 0; q < m; ++q) {
-        const int u = ord[q];
+    // the lower envelope in that order, the stack linked through below
+    int top = -1, n = 0;
+    int u = head;
+    for (int g = 0; g < m && DP_IN(u, P.n_u); ++g, u = s_ctrl[u].next) {
         const CtrlRec C = s_ctrl[u];
-        if (n > 0 && s_ctrl[stk[n - 1]].f == C.f)
+        if (n > 0 && s_ctrl[top].f == C.f)
             continue;  // same slope, not lower: never strictly below the kept line
         while (n >= 2) {
-            const CtrlRec A = s_ctrl[stk[n - 2]], B = s_ctrl[stk[n - 1]];
+            const int bu = top, au = s_ctrl[top].below;
+            if (!DP_IN(au, P.n_u))
+                break;
+            const CtrlRec A = s_ctrl[au], B = s_ctrl[bu];
             // B is redundant iff x(A, C) <= x(A, B):
             // (c_C - c_A)(f_A - f_B) <= (c_B - c_A)(f_A - f_C), denominators > 0
             const float lhs = __fmul_rn(__fsub_rn(C.cost, A.cost), __fsub_rn(A.f, B.f));
             const float rhs = __fmul_rn(__fsub_rn(B.cost, A.cost), __fsub_rn(A.f, C.f));
             const float tol = __fmul_rn(1e-5f, __fadd_rn(fabsf(lhs), fabsf(rhs)));
-            if (lhs < __fsub_rn(rhs, tol))
+            if (lhs < __fsub_rn(rhs, tol)) {
+                top = au;
                 --n;
-            else
+            } else {
                 break;
+            }
         }
-        if (DP_IN(n, MAX_MEMBERS))
-            stk[n++] = (short)u;
+        s_ctrl[u].below = (short)top;
+        top = u;
+        ++n;
     }
-    for (int q = 0; q < n; ++q)
-        s_ctrl[stk[q]].ok = 2;
+    for (int g = 0, q = top; g < n && DP_IN(q, P.n_u); ++g, q = s_ctrl[q].below)
+        s_ctrl[q].ok = 2;
     return n;
 }
 
@@ -301,7 +350,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         decode_u(P, u, ie, im, b);
         const int cu = class_of(P, ie, im, b);
         const ClassRec C = DP_IN(cu, P.n_cls) ? cls_row[cu] : ClassRec{};
-        CtrlRec r = {0.f, 0.f, 0, 0};
+        CtrlRec r = {0.f, 0.f, 0, 0, -1, -1};
         float I;
         const float Tm = node_val(P.tm_lo, P.tm_span, im, P.n_tm);
         const float Te = node_val(P.te_lo, P.te_span, ie, P.n_te);
@@ -309,7 +358,9 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         const bool engine_ok = !(stand && C.v1 == 0.f && C.dt == 0.f) || Te == 0.f;
         if (C.ok && engine_ok && torque_allowed(P, w, Te, Tm) && battery_current(P, w, Tm, I)) {
             const float dxi = __fdiv_rn(__fmul_rn(C.dt, I), P.cap);
-            snap_split(__fdiv_rn(-dxi, P.h_xi), r.d, r.f);
+            int d;
+            snap_split(__fdiv_rn(-dxi, P.h_xi), d, r.f);
+            r.d = (short)min(max(d, -32768), 32767);
             const float mf = fuel_rate(P, w, Te);
             r.cost = __fmul_rn(__fadd_rn(__fmul_rn(P.gamma, mf), one_m_gamma), C.dt);
             r.ok = 1;
@@ -363,7 +414,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
             const int b = c / (P.n_cls / P.n_b);
             for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
                 const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
-                const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
+                const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0, -1, -1};
                 nfeas += r.ok ? 1 : 0;
                 const int q = member_bucket(r);
                 if (q >= 0)
@@ -376,10 +427,10 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
         const unsigned long long first = (cnt * 0x0101010101ull) << 8;
         const int nspl = (int)((first >> 40) & 0xff);
         const int feas = nfeas > 0 ? 1 : 0;
-        int ent_tot, spl_tot, feas_tot;
-        const int ent_idx = block_exclusive_scan(feas, scan_buf, ent_tot) + ent_carry;
-        const int spl_off = block_exclusive_scan(nspl, scan_buf, spl_tot) + spl_carry;
-        block_exclusive_scan(nfeas, scan_buf, feas_tot);
+        int3 tot;
+        const int3 pre = block_exclusive_scan3(make_int3(feas, nspl, nfeas), scan_buf, tot);
+        const int ent_idx = pre.x + ent_carry, spl_off = pre.y + spl_carry;
+        const int ent_tot = tot.x, spl_tot = tot.y, feas_tot = tot.z;
         if (feas) {
             const int b = c / (P.n_cls / P.n_b);
             ClassEntry E;
@@ -393,7 +444,7 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
             unsigned long long next = first;  // byte q: next line of bucket q
             for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
                 const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
-                const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0};
+                const CtrlRec r = DP_IN(u, P.n_u) ? s_ctrl[u] : CtrlRec{0.f, 0.f, 0, 0, -1, -1};
                 const int q = member_bucket(r);
                 if (q < 0)
                     continue;
@@ -421,8 +472,9 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     }
 }
 
-// 5 CTAs per SM: the shared-memory limit of the paper-scale control table
-__global__ void __launch_bounds__(256, 5) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
+// 6 CTAs per SM: each holds the row's control table (16 bytes per control,
+// 31 KB at the paper-scale 1922 controls) in shared memory
+__global__ void __launch_bounds__(256, 6) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
                                                          int k_first, StageScratch sc)
 {
     extern __shared__ __align__(16) unsigned char pre_smem[];
