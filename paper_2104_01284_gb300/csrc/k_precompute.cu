@@ -182,7 +182,7 @@ __device__ int3 block_exclusive_scan3(int3 x, int *buf, int3 &total)
 
 // Shared per-control result.  next and below link the members of one (class,
 // shift bucket) into the sorted order and the envelope stack of
-// bucket_envelope (-1 ends a list): each control belongs to one bucket, and
+// class_envelopes (-1 ends a list): each control belongs to one bucket, and
 // one thread builds that bucket's lists.
 struct CtrlRec {
     float cost, f;
@@ -209,42 +209,19 @@ __device__ __forceinline__ bool line_before(const CtrlRec &o, int ou, const Ctrl
     return o.f > r.f || (o.f == r.f && (o.cost < r.cost || (o.cost == r.cost && ou < u)));
 }
 
-__device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, int d, CtrlRec *s_ctrl)
+// 16-bit field q of a packed word (signed: -1 ends a list)
+__device__ __forceinline__ int field16(unsigned long long w, int q) { return (int)(short)((w >> (16 * q)) & 0xffffu); }
+
+__device__ __forceinline__ unsigned long long with_field16(unsigned long long w, int q, int v)
 {
-    // the bucket's members sorted by (f desc, cost asc, u asc), linked
-    // through next.  Members arrive in decreasing engine torque: within a
-    // class and shift bucket the SoC fraction f falls with the motor share,
-    // so most append at the tail (O(1) each); the others walk from the head.
-    int head = -1, tail = -1, m = 0;
-    for (int ie = mem.ie_hi; ie >= mem.ie_lo; --ie) {
-        const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
-        if (!DP_IN(u, P.n_u))
-            continue;
-        const CtrlRec r = s_ctrl[u];
-        if (!r.ok || r.d != d)
-            continue;
-        ++m;
-        if (tail < 0 || line_before(s_ctrl[tail], tail, r, u)) {
-            s_ctrl[u].next = -1;
-            if (tail < 0)
-                head = u;
-            else
-                s_ctrl[tail].next = (short)u;
-            tail = u;
-            continue;
-        }
-        int prev = -1, cur = head;
-        for (int g = 0; g < m && DP_IN(cur, P.n_u) && line_before(s_ctrl[cur], cur, r, u); ++g) {
-            prev = cur;
-            cur = s_ctrl[cur].next;
-        }
-        s_ctrl[u].next = (short)cur;
-        if (prev < 0)
-            head = u;
-        else
-            s_ctrl[prev].next = (short)u;
-    }
-    // the lower envelope in that order, the stack linked through below
+    const int sh = 16 * q;
+    return (w & ~(0xffffull << sh)) | ((unsigned long long)(v & 0xffff) << sh);
+}
+
+// The lower envelope of one bucket's sorted list (head, m members), the
+// stack linked through below; marks its lines with ok = 2.
+__device__ int bucket_hull(const DevParams &P, int head, int m, CtrlRec *s_ctrl)
+{
     int top = -1, n = 0;
     int u = head;
     for (int g = 0; g < m && DP_IN(u, P.n_u); ++g, u = s_ctrl[u].next) {
@@ -275,6 +252,56 @@ __device__ int bucket_envelope(const DevParams &P, const Members &mem, int b, in
     for (int g = 0, q = top; g < n && DP_IN(q, P.n_u); ++g, q = s_ctrl[q].below)
         s_ctrl[q].ok = 2;
     return n;
+}
+
+// The lower envelopes of the four shift buckets d = -2 .. 1 of one torque
+// class (brake flag b): one pass over the members sorts each bucket's
+// feasible members by (f desc, cost asc, u asc) into a list linked through
+// next (heads, tails and counts packed per bucket), then each bucket's hull.
+// Members arrive in decreasing engine torque: within a class and shift
+// bucket the SoC fraction f falls with the motor share, so most append at
+// their list's tail (O(1) each); the others walk from the head.
+__device__ void class_envelopes(const DevParams &P, const Members &mem, int b, CtrlRec *s_ctrl)
+{
+    unsigned long long heads = ~0ull, tails = ~0ull;  // every list empty (-1)
+    unsigned counts = 0u;                              // 8 bits per bucket (< 256 members)
+    for (int ie = mem.ie_hi; ie >= mem.ie_lo; --ie) {
+        const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
+        if (!DP_IN(u, P.n_u))
+            continue;
+        const CtrlRec r = s_ctrl[u];
+        if (!r.ok || r.d < -2 || r.d > 1)
+            continue;
+        const int q = r.d + 2;
+        const int m = (int)((counts >> (8 * q)) & 0xffu) + 1;
+        counts += 1u << (8 * q);
+        const int tail = field16(tails, q);
+        if (tail < 0 || line_before(s_ctrl[tail], tail, r, u)) {
+            s_ctrl[u].next = -1;
+            if (tail < 0)
+                heads = with_field16(heads, q, u);
+            else
+                s_ctrl[tail].next = (short)u;
+            tails = with_field16(tails, q, u);
+            continue;
+        }
+        int prev = -1, cur = field16(heads, q);
+        for (int g = 0; g < m && DP_IN(cur, P.n_u) && line_before(s_ctrl[cur], cur, r, u); ++g) {
+            prev = cur;
+            cur = s_ctrl[cur].next;
+        }
+        s_ctrl[u].next = (short)cur;
+        if (prev < 0)
+            heads = with_field16(heads, q, u);
+        else
+            s_ctrl[prev].next = (short)u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int m = (int)((counts >> (8 * q)) & 0xffu);
+        if (m > 0)
+            bucket_hull(P, field16(heads, q), m, s_ctrl);
+    }
 }
 
 // Tables of speed row i of stage k (one CTA of 256 threads; P in shared memory).
@@ -369,23 +396,21 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     }
     __syncthreads();
 
-    // 3. the lower envelope of every (class, SoC-shift bucket d in
-    // {-2, -1, 0, 1}) pair, one pair per task (members are disjoint).  An
-    // envelope costs ~m^2 for m members: tasks are ranked by decreasing class
-    // size (the total torques nearest the middle of their range first) and
-    // dealt out in a snake, so a thread's heavy task of one round pairs with
-    // a light one of the next.
+    // 3. the lower envelopes of every class's SoC-shift buckets d in {-2, -1,
+    // 0, 1}, one class per task (members are disjoint).  Tasks are ranked by
+    // decreasing class size (the total torques nearest the middle of their
+    // range first) and dealt out in a snake, so a thread's heavy task of one
+    // round pairs with a light one of the next.
     const int n_sum = P.n_cls / P.n_b;
     for (int k = 0;; ++k) {
         const int task = k * blockDim.x + ((k & 1) ? blockDim.x - 1 - threadIdx.x : threadIdx.x);
-        if (k * blockDim.x >= P.n_cls * 4)
+        if (k * blockDim.x >= P.n_cls)
             break;
-        if (task >= P.n_cls * 4)
+        if (task >= P.n_cls)
             continue;
-        const int rank = task >> 2, bucket = task & 3;
-        const int b = rank % P.n_b, q = rank / P.n_b, mid = (n_sum - 1) / 2;
+        const int b = task % P.n_b, q = task / P.n_b, mid = (n_sum - 1) / 2;
         const int c = b * n_sum + mid + ((q & 1) ? (q + 1) / 2 : -(q / 2));
-        bucket_envelope(P, class_members(P, c), b, bucket - 2, s_ctrl);
+        class_envelopes(P, class_members(P, c), b, s_ctrl);
     }
     __syncthreads();
 
