@@ -306,6 +306,18 @@ dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5]);
  * one exists for cross-checking.  DP_ERR_INVALID_ARG otherwise. */
 dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant);
 
+/* Lower envelopes of the stage tables (Sec. IV's per-(v, u) table, reduced):
+ * within one torque class and SoC-shift bucket every control's value at a
+ * state is G + (c_u + f_u D) for the same two blended values of J_{k+1}
+ * (Eq. 9b), a line in D, so only the lines on the bucket's lower envelope can
+ * be the minimum.  on = 1 (default) keeps only those lines (a line is dropped
+ * only when it lies above two others by a clear margin); on = 0 keeps every
+ * feasible control, a cross-check: the values and policies of a solve are the
+ * same either way (FP32 evaluations of a dropped line never fall below the
+ * kept ones).  Takes effect at the next solve; call it between solves, not
+ * while one runs.  Synchronous; DP_ERR_INVALID_ARG for another value. */
+dp_status dp_set_envelopes(dp_problem_t p, int32_t on);
+
 /* Profiling hook: run one backward sweep (same work and results as
  * dp_solve_backward) with direct launches and CUDA events around every
  * kernel, synchronise, and report milliseconds: ms[0] terminal values,

@@ -273,6 +273,7 @@ void fill_params(const dp_problem_desc *d, DevParams &P)
     for (int q = 0; q < 3; ++q)
         P.te_max_c[q] = d->torque_limits ? f32(d->te_max_coef[q]) : 0.f;
     P.bsg_pmax = d->torque_limits ? f32(d->bsg_power_max) : 0.f;
+    P.all_lines = 0;
 }
 
 void fill_tables(const dp_problem_desc *d, HostTables &t)
@@ -699,6 +700,7 @@ dp_status dp_problem_update(dp_problem_t p, const dp_problem_desc *desc, void *s
     fill_params(desc, P);
     if (P.n_cls != p->hP.n_cls)
         return fail(DP_ERR_INVALID_ARG, "update changes the torque class structure");
+    P.all_lines = p->hP.all_lines;  // a setting of the problem object, not of the descriptor
     p->hP = P;
     p->n_lights = desc->n_lights;
     fill_tables(desc, p->h);
@@ -784,6 +786,23 @@ dp_status dp_set_kernel_variant(dp_problem_t p, int32_t variant)
         if (p->gexec)
             cudaGraphExecDestroy(p->gexec);
         p->gexec = nullptr;
+    }
+    return DP_OK;
+}
+
+dp_status dp_set_envelopes(dp_problem_t p, int32_t on)
+{
+    if (!p || (on != 0 && on != 1))
+        return fail(DP_ERR_INVALID_ARG, "on must be 0 or 1");
+    if (p->hP.all_lines != 1 - on) {
+        p->hP.all_lines = 1 - on;
+        DP_CUDA(cudaMemcpyAsync(p->dP, &p->hP, sizeof(DevParams), cudaMemcpyHostToDevice, p->create_stream));
+        DP_CUDA(cudaStreamSynchronize(p->create_stream));
+        if (p->gexec)
+            cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        p->solved = false;
+        p->rollout_may_overlap = false;
     }
     return DP_OK;
 }

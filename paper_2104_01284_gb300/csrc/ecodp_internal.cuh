@@ -107,6 +107,7 @@ struct DevParams {
     int light_model;    // 1: green indicator sampled on the time grid
     int torque_limits;  // 1: speed-dependent torque limits
     float te_max_c[3], bsg_pmax;
+    int all_lines;  // 1: the tables keep every feasible control of each SoC-shift bucket (no envelope)
 };
 
 // Speed-dependent torque limits (Eq. 7e, 7f) at crank speed w; true if the

@@ -410,7 +410,17 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
             continue;
         const int b = task % P.n_b, q = task / P.n_b, mid = (n_sum - 1) / 2;
         const int c = b * n_sum + mid + ((q & 1) ? (q + 1) / 2 : -(q / 2));
-        class_envelopes(P, class_members(P, c), b, s_ctrl);
+        const Members mem = class_members(P, c);
+        if (!P.all_lines) {
+            class_envelopes(P, mem, b, s_ctrl);
+            continue;
+        }
+        // the cross-check setting: every feasible member of a bucket is a line
+        for (int ie = mem.ie_lo; ie <= mem.ie_hi; ++ie) {
+            const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
+            if (DP_IN(u, P.n_u) && s_ctrl[u].ok && s_ctrl[u].d >= -2 && s_ctrl[u].d <= 1)
+                s_ctrl[u].ok = 2;
+        }
     }
     __syncthreads();
 

@@ -115,6 +115,9 @@ EXPORTED.append("dp_debug_checks")
 dp_measure_fp32_peak = _sig("dp_measure_fp32_peak", C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.c_void_p)
 EXPORTED.append("dp_measure_fp32_peak")
+# lower envelopes of the stage tables on (default) or off (every line kept)
+dp_set_envelopes = _sig("dp_set_envelopes", C.c_void_p, C.c_int32)
+EXPORTED.append("dp_set_envelopes")
 # on-chip load bandwidth probes (shared memory, L1, L2)
 dp_measure_onchip_bw = _sig("dp_measure_onchip_bw", C.c_int32, C.c_int32, C.POINTER(C.c_double),
                             C.POINTER(C.c_double), C.c_void_p)

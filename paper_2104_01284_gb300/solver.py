@@ -144,6 +144,13 @@ class EcoDP:
         N.check(N.dp_set_kernel_variant(self.h, {"direct": 0, "tiled": 1, "tiled8": 2, "tiled6": 3}[variant]),
                 "dp_set_kernel_variant")
 
+    def set_envelopes(self, on: bool = True):
+        """Keep only each (torque class, SoC-shift bucket)'s lower envelope
+        of lines in the stage tables (default), or every feasible control
+        (a cross-check with the same results)."""
+        with torch.cuda.device(self.device):
+            N.check(N.dp_set_envelopes(self.h, 1 if on else 0), "dp_set_envelopes")
+
     # -- compute ------------------------------------------------------------
     def solve(self, stream=None):
         with torch.cuda.device(self.device):

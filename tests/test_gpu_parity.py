@@ -106,6 +106,32 @@ def test_tiled_and_direct_bit_identical(gpu, name):
         a.close()
 
 
+@pytest.mark.parametrize("name", list(PROBLEMS) + ["paper_scale"])
+def test_envelopes_keep_every_minimum(gpu, name):
+    """Within a torque class and SoC-shift bucket every control's value at a
+    state is a line in the SoC difference of J_{k+1} (Eq. 9b), and the stage
+    tables keep only each bucket's lower envelope.  The envelope drops only
+    lines that can never give a state's minimum: with every feasible control
+    kept (dp_set_envelopes(0)) the sweep returns bit-identical values and
+    policies at every stage, in the tiled kernel and (below paper scale) in
+    the direct one."""
+    p = P.config1(seed=1) if name == "paper_scale" else PROBLEMS[name]()
+    for variant in ("tiled",) if name == "paper_scale" else ("tiled", "direct"):
+        a = gpu(p)
+        a.set_variant(variant)
+        a.solve()
+        b = gpu(p)
+        b.set_variant(variant)
+        b.set_envelopes(False)
+        b.solve()
+        for k in range(p.n_stages + 1):
+            assert torch.equal(a.value(k), b.value(k)), (variant, k)
+            if k < p.n_stages:
+                assert torch.equal(a.policy(k), b.policy(k)), (variant, k)
+        a.close()
+        b.close()
+
+
 @pytest.mark.parametrize("variant,n_t", [("tiled", 201), ("tiled6", 201), ("tiled", 101), ("tiled", 45),
                                          ("tiled", 62), ("tiled", 254)])
 def test_unsplit_tiled_sweep_bit_identical(gpu, variant, n_t):
