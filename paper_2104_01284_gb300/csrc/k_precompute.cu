@@ -264,7 +264,7 @@ __device__ int bucket_hull(const DevParams &P, int head, int m, CtrlRec *s_ctrl)
 __device__ void class_envelopes(const DevParams &P, const Members &mem, int b, CtrlRec *s_ctrl)
 {
     unsigned long long heads = ~0ull, tails = ~0ull;  // every list empty (-1)
-    unsigned counts = 0u;                              // 8 bits per bucket (< 256 members)
+    unsigned counts = 0u;  // 8 bits per bucket: a class has at most min(n_te, n_tm) <= 90 members (8192 controls)
     for (int ie = mem.ie_hi; ie >= mem.ie_lo; --ie) {
         const int u = (ie * P.n_tm + member_im(mem, ie)) * P.n_b + b;
         if (!DP_IN(u, P.n_u))
