@@ -304,7 +304,7 @@ __device__ void class_envelopes(const DevParams &P, const Members &mem, int b, C
     }
 }
 
-// Tables of speed row i of stage k (one CTA of 256 threads; P in shared memory).
+// Tables of speed row i of stage k (one CTA; P in shared memory).
 __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k, int i, const StageScratch &sc,
                                CtrlRec *s_ctrl, int *scan_buf)
 {
@@ -507,9 +507,10 @@ __device__ void precompute_row(const DevParams &P, const StageTables &tb, int k,
     }
 }
 
-// 6 CTAs per SM: each holds the row's control table (16 bytes per control,
-// 31 KB at the paper-scale 1922 controls) in shared memory
-__global__ void __launch_bounds__(256, 6) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
+// 128 threads (the per-class phases keep ~1 class per thread busy at the
+// paper-scale 122 classes) and 7 CTAs per SM: each holds the row's control
+// table (16 bytes per control, 31 KB at 1922 controls) in shared memory
+__global__ void __launch_bounds__(128, 7) precompute_kernel(const DevParams *__restrict__ dP, StageTables tb,
                                                          int k_first, StageScratch sc)
 {
     extern __shared__ __align__(16) unsigned char pre_smem[];
@@ -619,7 +620,7 @@ cudaError_t launch_precompute(const DevParams *dP, const DevParams &hP, StageTab
     cudaError_t err = cudaFuncSetAttribute(precompute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess)
         return err;
-    precompute_kernel<<<dim3(hP.n_v, n_k), 256, smem, s>>>(dP, tb, k_first, sc);
+    precompute_kernel<<<dim3(hP.n_v, n_k), 128, smem, s>>>(dP, tb, k_first, sc);
     return cudaGetLastError();
 }
 
