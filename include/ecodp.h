@@ -149,7 +149,11 @@ dp_status dp_problem_destroy(dp_problem_t p);
  * (a torque class) and the same SoC cell shift read the same two SoC rows of
  * J_{k+1}; their values are lines c + f D in the difference D of those rows,
  * and only the lines on the lower envelope of each such group are evaluated
- * (the minimum is that of all controls up to FP32 rounding).  Exact FP32 ties
+ * (the FP32 minimum is that of all controls, see dp_set_envelopes).  Successor
+ * times never precede the state's own time, so a state whose time node lies
+ * beyond the last time column of J_{k+1} holding a feasible value reads only
+ * infeasible values: the tiled kernel writes such states infeasible without
+ * evaluating them, warp by warp (the result is the same).  Exact FP32 ties
  * are broken in the order (torque class, control index): the first class,
  * ordered by brake flag and then by ascending total torque, that reaches the
  * minimum, then the lowest control index inside that class.  Asynchronous on stream;
@@ -327,15 +331,17 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4]);
 
 /* Counters of the last sweep (synchronises the stream): out[0] = state x
  * control evaluations whose control passed the per-(speed, control) checks
- * (effective evaluations, summed over stages), out[1] = state x torque-class
- * pairs evaluated, out[2] = bytes one dp_problem_update copies host to
- * device, out[3] = bytes one dp_rollout copies device to host, out[4] =
- * reserved (0), out[5] = feasible states whose argmin the
+ * (effective evaluations, summed over stages and over every state), out[1] =
+ * state x torque-class pairs evaluated, out[2] = bytes one dp_problem_update
+ * copies host to device, out[3] = bytes one dp_rollout copies device to
+ * host, out[4] = reserved (0), out[5] = feasible states whose argmin the
  * tiled kernel recovered, out[6] = state x control pairs the Bellman kernels
  * evaluate: per torque class and SoC shift only the controls on the lower
- * envelope of their values (see dp_solve_backward).  DP_ERR_NOT_SOLVED
- * before a sweep. */
-dp_status dp_sweep_stats(dp_problem_t p, int64_t out[7], void *stream);
+ * envelope of their values, out[7] = (state, stage) pairs written infeasible
+ * without evaluation because their time lies beyond J_{k+1}'s last feasible
+ * time column (out[1] and out[6] exclude them; see dp_solve_backward).
+ * DP_ERR_NOT_SOLVED before a sweep. */
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[8], void *stream);
 
 /* ---- Batches of independent problems ------------------------------------
  *

@@ -71,6 +71,7 @@ struct dp_problem {
     double *d_roll = nullptr;
     int *d_roll_u = nullptr;
     unsigned long long *d_stats = nullptr;
+    int *d_lmax = nullptr;  // [N + 1] last feasible time column per stage of the last sweep
     double *d_lam = nullptr;  // adjoint weights of two consecutive stages
     int *d_front = nullptr;   // adjoint support lists (AdjFrontier)
     unsigned *d_fbits = nullptr;
@@ -463,8 +464,20 @@ dp_status upload_tables(dp_problem *p, cudaStream_t s)
 // the other paths ignore them).
 cudaError_t sweep_stage(dp_problem *p, int k, cudaStream_t s)
 {
-    return launch_bellman(p->dP, p->hP, p->tables(), k, p->scratch(), p->Vsweep(k + 1), p->Vsweep(k), p->pi(k),
-                          p->variant, s, p->quad(k + 1), p->quad(k));
+    StageScratch sc = p->scratch();
+    sc.lmax = p->d_lmax;  // J_{k+1}'s last feasible time column in, J_k's out
+    return launch_bellman(p->dP, p->hP, p->tables(), k, sc, p->Vsweep(k + 1), p->Vsweep(k), p->pi(k), p->variant, s,
+                          p->quad(k + 1), p->quad(k));
+}
+
+// Counters and per-stage time limits reset before a sweep (memset nodes when
+// the sweep is captured).
+cudaError_t sweep_reset(dp_problem *p, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(p->d_stats, 0, 8 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p->d_lmax, 0xff, (size_t)(p->N + 1) * sizeof(int), s);
+    return e;
 }
 
 // The backward sweep's launches: terminal values (and their corner quads),
@@ -472,7 +485,7 @@ cudaError_t sweep_stage(dp_problem *p, int k, cudaStream_t s)
 // then the N Bellman stages in backward order.
 dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 {
-    DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
+    DP_CUDA(sweep_reset(p, s));
     DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(p->N), s));
     if (p->d_quad)
         DP_CUDA(launch_quad_from_pad(p->hP, p->Vsweep(p->N), p->quad(p->N), s));
@@ -649,7 +662,8 @@ dp_status dp_problem_create(const dp_problem_desc *desc, const dp_allocator *all
     TRY(dev_alloc_n(p, p->pi_elems, &p->d_pi_tmp));
     TRY(dev_alloc_n(p, (size_t)(3 * (P.N + 1) + 3 * P.N + 4), &p->d_roll));
     TRY(dev_alloc_n(p, (size_t)P.N, &p->d_roll_u));
-    TRY(dev_alloc_n(p, (size_t)5, &p->d_stats));
+    TRY(dev_alloc_n(p, (size_t)8, &p->d_stats));
+    TRY(dev_alloc_n(p, (size_t)p->N + 1, &p->d_lmax));
     TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_lam));
     TRY(dev_alloc_n(p, 2 * p->pi_elems, &p->d_front));
     TRY(dev_alloc_n(p, 2 * ((p->pi_elems + 31) / 32), &p->d_fbits));
@@ -731,24 +745,25 @@ dp_status dp_problem_sizes(dp_problem_t p, int32_t sizes[5])
     return DP_OK;
 }
 
-dp_status dp_sweep_stats(dp_problem_t p, int64_t out[7], void *stream)
+dp_status dp_sweep_stats(dp_problem_t p, int64_t out[8], void *stream)
 {
     if (!p || !out)
         return fail(DP_ERR_INVALID_ARG, "NULL argument");
     if (!p->solved)
         return fail(DP_ERR_NOT_SOLVED, "call dp_solve_backward first");
-    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaStream_t s = (cudaStream_t)stream;
     DP_CUDA(cudaMemcpyAsync(h, p->d_stats, sizeof h, cudaMemcpyDeviceToHost, s));
     DP_CUDA(cudaStreamSynchronize(s));
     out[0] = (int64_t)h[0] * p->n_xi * p->n_t;
-    out[1] = (int64_t)h[1] * p->n_xi * p->n_t;
+    out[1] = (int64_t)h[1] * p->n_xi * p->n_t - (int64_t)h[5];
     // bytes of one dp_problem_update (tables) and one dp_rollout (trajectory)
     out[2] = (int64_t)(sizeof(DevParams) + p->h.bytes());
     out[3] = (int64_t)((3 * (p->N + 1) + 3 * p->N + 4) * sizeof(double) + p->N * sizeof(int));
     out[4] = (int64_t)h[2];
     out[5] = (int64_t)h[3];
-    out[6] = (int64_t)h[4] * p->n_xi * p->n_t;
+    out[6] = (int64_t)h[4] * p->n_xi * p->n_t - (int64_t)h[6];
+    out[7] = (int64_t)h[7];
     return DP_OK;
 }
 
@@ -862,7 +877,7 @@ dp_status dp_profile_sweep(dp_problem_t p, void *stream, float ms[4])
         DP_CUDA(cudaEventCreate(&e));
     dp_status st = DP_OK;
     auto run = [&]() -> dp_status {
-        DP_CUDA(cudaMemsetAsync(p->d_stats, 0, 5 * sizeof(unsigned long long), s));
+        DP_CUDA(sweep_reset(p, s));
         DP_CUDA(cudaEventRecord(ev[0], s));
         DP_CUDA(launch_terminal(p->dP, p->hP, p->Vsweep(N), s));
         if (p->d_quad)

@@ -449,6 +449,7 @@ dp_status dp_multi_create(const dp_problem_desc *descs, int32_t n, const dp_mult
         TRY(m_alloc_n(m, rows * P.n_u, &I.sc.spl));
         I.sc.stats = nullptr;
         I.sc.part = nullptr;
+        I.sc.lmax = nullptr;
         m->out_off[b] = m->out_total;
         m->out_total += (long long)roll_doubles(P.N);
         m->u_off[b] = m->u_total;

@@ -571,6 +571,49 @@ __host__ __device__ inline int chunks_per_row(int n_xi, int n_t)
 // the argmin from `part`.
 constexpr int TILE_FULL = 0, TILE_SLICE = 1;
 
+// Relative cost of one class in the tile's loop: the window and bookkeeping
+// (about 24 line evaluations' worth) plus its lines.
+__device__ __forceinline__ int class_cost(const TileClass &T)
+{
+    return 24 + T.nb0 + T.nb1 + T.nb2 + (int)(T.nb3_other & 0xffffu) + (int)(T.nb3_other >> 16);
+}
+
+// Slice s of S of the classes [0, n): contiguous, of about equal cost (slice
+// t starts at the first class whose inclusive cost prefix exceeds t/S of the
+// total).  Called by a whole warp; every lane gets the same bounds.
+__device__ __forceinline__ void slice_bounds(const TileClass *s_tc, int n, int S, int s, int lane, int &lo, int &hi)
+{
+    int tot = 0;
+    for (int b = 0; b < n; b += 32)
+        tot += __reduce_add_sync(FULL, b + lane < n ? class_cost(s_tc[b + lane]) : 0);
+    auto boundary = [&](int t) -> int {
+        if (t <= 0)
+            return 0;
+        if (t >= S)
+            return n;
+        const long long target = (long long)tot * t / S;
+        long long run = 0;
+        for (int b = 0; b < n; b += 32) {
+            const int e = b + lane;
+            const int c = e < n ? class_cost(s_tc[e]) : 0;
+            int incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d)
+                    incl += y;
+            }
+            const unsigned m = __ballot_sync(FULL, e < n && run + incl > target);
+            if (m)
+                return b + __ffs((int)m) - 1;
+            run += __shfl_sync(FULL, incl, 31);
+        }
+        return n;
+    };
+    lo = boundary(s);
+    hi = boundary(s + 1);
+}
+
 __device__ __forceinline__ unsigned long long pack_min(float v, int e)
 {
     const float z = __fadd_rn(v, 0.f);  // -0 -> +0
@@ -583,15 +626,101 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
                              float *__restrict__ Vk, int16_t *__restrict__ pik, int i, int chunk,
                              unsigned char *smem_raw, unsigned long long *stats, int e_begin = 0, int e_end = 0,
                              unsigned long long *__restrict__ part = nullptr, const float4 *__restrict__ Qn = nullptr,
-                             float4 *__restrict__ Qk = nullptr)
+                             float4 *__restrict__ Qk = nullptr, int lmax_next = INT_MAX, int *lmax_out = nullptr,
+                             int n_chunks = 0)
 {
     const int tid = threadIdx.x;
     const Layout L = layout<R>(P.n_cls, P.n_u);
     TileClass *s_tc = reinterpret_cast<TileClass *>(smem_raw);
     unsigned *s_dtv = reinterpret_cast<unsigned *>(smem_raw + L.dtv);
     float2 *s_line = reinterpret_cast<float2 *>(smem_raw + L.line);
+    const int warp = tid >> 5, lane = tid & 31;
+    const int n_jg = (P.n_xi + R - 1) / R;
+    // Every successor time is at least the state's own (time shifts and
+    // waits are non-negative), so past J_{k+1}'s last feasible time column
+    // (lmax_next, with n_chunks the row's tiles in this launch; single-problem
+    // sweeps only) every corner a state reads is infeasible, and so is the
+    // state: the lanes cover only the n_tc time columns up to it, and the
+    // states past them are written infeasible without evaluation.
+    int n_tc = P.n_t;
+    if constexpr (MODE == TILE_FULL && NC) {
+        if (n_chunks > 0 && lmax_next < P.n_t - 1)
+            n_tc = max(lmax_next + 1, 0);
+    }
+    const int n_act = n_jg * n_tc;  // lanes (SoC group, time column) of the row
+    // With fewer lanes, the classes of a lane group may be split over S warps
+    // (contiguous class slices, merged in class order after the loop) as long
+    // as the row's lanes stay within its n_chunks tiles: a warp's class loop
+    // is a chain of dependent instructions, and S warps finish it sooner.
+    int S = 1;
+    if constexpr (MODE == TILE_FULL && NC) {
+        if (n_tc < P.n_t) {
+            if ((4 * n_act + TLANES - 1) / TLANES <= n_chunks)
+                S = 4;
+            else if ((2 * n_act + TLANES - 1) / TLANES <= n_chunks)
+                S = 2;
+        }
+    }
+    const int grp = warp / S, slice = warp - grp * S;   // lane group (32 lanes), class slice
+    const int chunk0 = chunk * (TLANES / S) + grp * 32;  // first lane of this warp's group
+    const int f_raw = chunk0 + lane;
+    const bool f_ok = f_raw < n_act;
+    const int f = f_ok ? f_raw : max(n_act - 1, 0);
+    const int jg = n_tc > 0 ? f / n_tc : 0;
+    const int l = f - jg * n_tc;
+    const int jb = jg * R;
+    const bool tile_active = chunk * (TLANES / S) < n_act;  // uniform over the CTA
+    const int qrows = quad_rows(P.n_xi);
+    const size_t vrowq = (size_t)qrows * QLD;
+    // J_k's value val at state (j, lj) of row i, -1 as policy where
+    // infeasible, and the value in the corner quads that hold it: (i, j,
+    // lj).x, (i, j, lj - 1).y, (i - 1, j, lj).z, (i - 1, j, lj - 1).w
+    auto store = [&](int j, int lj, float val, bool feas) {
+        const size_t ov = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + lj;
+        const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + lj;
+        if (!DP_IN(ov, (size_t)P.n_v * P.xi_rows * P.ld_t) || !DP_IN(op, (size_t)P.n_v * P.n_xi * P.n_t))
+            return;
+        Vk[ov] = val;
+        if (!feas)
+            pik[op] = -1;
+        if (QLD > 0) {
+            float *qf = reinterpret_cast<float *>(Qk);
+            const size_t oq = ((size_t)i * qrows + (j + QUAD_PAD)) * QLD + lj;
+            if (DP_IN(oq, (size_t)P.n_v * vrowq)) {
+                qf[4 * oq] = val;
+                if (lj > 0)
+                    qf[4 * (oq - 1) + 1] = val;
+                if (i > 0) {
+                    qf[4 * (oq - vrowq) + 2] = val;
+                    if (lj > 0)
+                        qf[4 * (oq - vrowq - 1) + 3] = val;
+                }
+            }
+        }
+    };
     __syncthreads();  // the previous tile may still read the tables
-    {
+    if (MODE == TILE_FULL && NC && n_tc < P.n_t) {
+        // the row's states past the last time column that can be feasible,
+        // shared out over the row's tiles
+        const int w_t = P.n_t - n_tc, n_fill = P.n_xi * w_t;
+        unsigned n_filled = 0;
+        for (int q = chunk * TLANES + tid; q < n_fill; q += n_chunks * TLANES) {
+            const int j = q / w_t;
+            store(j, n_tc + (q - j * w_t), V_BIG, false);
+            ++n_filled;
+        }
+        if (stats) {
+            // the (state, class) and (state, line) pairs the tables would
+            // have cost these states
+            const unsigned n = __reduce_add_sync(FULL, n_filled);
+            if (lane == 0 && n > 0) {
+                atomicAdd(stats + 5, (unsigned long long)n * (unsigned long long)max(n_ent, 0));
+                atomicAdd(stats + 6, (unsigned long long)n * (unsigned long long)max(n_spl, 0));
+                atomicAdd(stats + 7, (unsigned long long)n);
+            }
+        }
+    }
+    if (tile_active) {
         // a slice stages only its own classes and their lines (same indices)
         int c_lo = 0, c_hi = n_ent, q_lo = 0, q_hi = n_spl;
         if (MODE == TILE_SLICE) {
@@ -617,22 +746,13 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             if (DP_IN(q, P.n_u))
                 s_line[q] = __ldcs(reinterpret_cast<const float2 *>(g_spl + q));
     }
-    const int warp = tid >> 5, lane = tid & 31;
     unsigned char *wbase = smem_raw + L.warp + warp * L.warp_bytes;
     int *w_cnt = reinterpret_cast<int *>(wbase);
     unsigned *w_list = reinterpret_cast<unsigned *>(wbase + L.w_list);
     float *w_best = reinterpret_cast<float *>(wbase + L.w_best);
     __syncthreads();
+    const bool warp_idle = !__any_sync(FULL, f_ok);
 
-    const int n_jg = (P.n_xi + R - 1) / R;
-    const int n_flat = n_jg * P.n_t;
-    const int chunk0 = chunk * TLANES + warp * 32;  // first flat index of this warp
-    const int f_raw = chunk0 + lane;
-    const bool f_ok = f_raw < n_flat;
-    const int f = f_ok ? f_raw : n_flat - 1;
-    const int jg = f / P.n_t;
-    const int l = f - jg * P.n_t;
-    const int jb = jg * R;
     const float one_m_gamma = __fsub_rn(1.f, P.gamma);
     const float v = node_val(P.v_lo, P.v_span, i, P.n_v);
     const StageInfo si = stage_info(tb, k, v);
@@ -645,8 +765,6 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         roff[w] = row_offset(P, jb - 2 + w);
     // corner quads (QLD > 0): the lane's window row w = 0 (SoC row jb - 2) is
     // quad row jb - 2 + QUAD_PAD of every speed row
-    const int qrows = quad_rows(P.n_xi);
-    const size_t vrowq = (size_t)qrows * QLD;
     const float4 *qlane = QLD > 0 ? Qn + (size_t)(jb - 2 + QUAD_PAD) * QLD : nullptr;
 
     // per row: the running minimum and the first class (in class order)
@@ -658,8 +776,10 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         best[r] = __int_as_float(0x7f800000);
         bcls[r] = 0;
     }
-    const int e_lo = MODE == TILE_SLICE ? e_begin : 0;
-    const int e_hi = MODE == TILE_SLICE ? min(e_end, n_ent) : n_ent;
+    int e_lo = MODE == TILE_SLICE ? e_begin : 0;
+    int e_hi = MODE == TILE_SLICE ? min(e_end, n_ent) : n_ent;
+    if (MODE == TILE_FULL && NC && S > 1)
+        slice_bounds(s_tc, min(n_ent, P.n_cls), S, slice, lane, e_lo, e_hi);
     // Consecutive classes with the same speed cell and time shift read the
     // same four corners of J_{k+1} and differ only in their weights.  Where
     // the corners depend neither on the class nor on the lane (no red check
@@ -668,7 +788,7 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
     const bool can_pair = !si.wait_row && !(P.light_model != 1 && si.next_light >= 0);
     float H[R + 4];
     bool have_h = false;
-    for (int e = e_lo; e < e_hi; ++e) {
+    for (int e = warp_idle ? e_hi : e_lo; e < e_hi; ++e) {
         if (!DP_IN(e, P.n_cls))
             break;
         const TileClass T = s_tc[e];
@@ -777,6 +897,34 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         }
     }
 
+    if (MODE == TILE_FULL && NC && S > 1) {
+        // slices s > 0 hand their minima to slice 0 through their own
+        // argmin-recovery buffers; a later slice's classes come later in
+        // class order, so a strict < keeps the first class on exact ties
+        if (slice > 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                w_best[lane * R + r] = best[r];
+                w_list[lane * R + r] = (unsigned)bcls[r];
+            }
+        }
+        __syncthreads();
+        if (slice > 0)
+            return;
+        for (int s2 = 1; s2 < S; ++s2) {
+            const unsigned char *ob = smem_raw + L.warp + (warp + s2) * L.warp_bytes;
+            const float *o_best = reinterpret_cast<const float *>(ob + L.w_best);
+            const unsigned *o_cls = reinterpret_cast<const unsigned *>(ob + L.w_list);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float vb = o_best[lane * R + r];
+                if (vb < best[r]) {
+                    best[r] = vb;
+                    bcls[r] = (int)o_cls[lane * R + r];
+                }
+            }
+        }
+    }
     if (MODE == TILE_SLICE) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -798,35 +946,19 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
         const bool feas = valid && !masked && best[r] < V_FEAS_MAX;
         if (feas)
             todo |= 1u << r;
-        const size_t ov = ((size_t)i * P.xi_rows + (j + 1)) * P.ld_t + l;
-        const size_t op = ((size_t)i * P.n_xi + j) * P.n_t + l;
-        if (valid && DP_IN(ov, (size_t)P.n_v * P.xi_rows * P.ld_t) && DP_IN(op, (size_t)P.n_v * P.n_xi * P.n_t)) {
-            const float val = feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG;
-            Vk[ov] = val;
-            if (!feas)
-                pik[op] = -1;
-            if (QLD > 0) {
-                // J_k's value in the quads that hold it: (i, j, l).x,
-                // (i, j, l - 1).y, (i - 1, j, l).z, (i - 1, j, l - 1).w
-                float *qf = reinterpret_cast<float *>(Qk);
-                const size_t oq = ((size_t)i * qrows + (j + QUAD_PAD)) * QLD + l;
-                if (DP_IN(oq, (size_t)P.n_v * vrowq)) {
-                    qf[4 * oq] = val;
-                    if (l > 0)
-                        qf[4 * (oq - 1) + 1] = val;
-                    if (i > 0) {
-                        qf[4 * (oq - vrowq) + 2] = val;
-                        if (l > 0)
-                            qf[4 * (oq - vrowq - 1) + 3] = val;
-                    }
-                }
-            }
-        }
+        if (valid)
+            store(j, l, feas ? __fadd_rn(best[r], __fmul_rn(one_m_gamma, wait)) : V_BIG, feas);
     }
     if (stats) {
         const unsigned n_find = __reduce_add_sync(FULL, (unsigned)__popc(todo));
         if (lane == 0)
             atomicAdd(stats + 3, (unsigned long long)n_find);
+    }
+    if (lmax_out) {
+        // J_k's last feasible time column, for the next stage's skip
+        const int lm = __reduce_max_sync(FULL, todo ? l : -1);
+        if (lane == 0 && lm >= 0)
+            atomicMax(lmax_out, lm);
     }
 
     // bucket the feasible states by their first winning class and recover the
@@ -879,8 +1011,8 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             continue;
         const int ln = s / R, r = s - ln * R;
         const int fq = chunk0 + ln;
-        const int jgq = fq / P.n_t;
-        const int lq = fq - jgq * P.n_t;
+        const int jgq = fq / n_tc;
+        const int lq = fq - jgq * n_tc;
         const float tlq = node_val(P.t_lo, P.t_span, lq, P.n_t);
         const float wq = wait_time(tb, k, tlq, si.wait_row);
         const TileClass T = s_tc[e];

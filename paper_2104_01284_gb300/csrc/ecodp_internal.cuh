@@ -306,13 +306,19 @@ struct StageScratch {
     ClassEntry *ent;  // [slots][n_v][n_cls]
     int *row_cnt;     // [slots][n_v][2] feasible classes, splits
     SplitRec *spl;    // [slots][n_v][n_u]
-    // [5] running totals (may be NULL): feasible (v, u) pairs, feasible
+    // [8] running totals (may be NULL): feasible (v, u) pairs, feasible
     // (v, class) pairs, states whose minimum ties across classes, states
-    // whose argmin was recovered, (v, u) pairs kept in the tables (envelopes)
+    // whose argmin was recovered, (v, u) pairs kept in the tables (envelopes);
+    // of the states skipped as infeasible (below): (state, class) pairs,
+    // (state, line) pairs, states
     unsigned long long *stats;
     // [n_v][n_soc][n_t] packed per-state minima of the class-split Bellman
     // launch (all ones between stages); NULL: never split
     unsigned long long *part;
+    // [N + 1] per stage of a sweep: the last time column of J_k holding a
+    // feasible state (-1: none; all -1 before the sweep, J_N's is n_t - 1
+    // without an entry).  NULL: the launch neither reads nor writes it.
+    int *lmax;
 };
 
 // One instance of a batch (device-resident descriptor).

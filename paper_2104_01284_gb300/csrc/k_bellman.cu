@@ -102,9 +102,18 @@ __global__ void __launch_bounds__(TLANES, tile_minb<R>())
     // come last and fill the SMs that received a fourth CTA
     const int i = gridDim.y - 1 - blockIdx.y;
     const size_t row = (size_t)k * P.n_v + i;
+    // in a sweep: J_{k+1}'s last feasible time column (J_N is finite
+    // everywhere), and J_k's to record
+    int lmax_next = INT_MAX;
+    int *lmax_out = nullptr;
+    if (sc.lmax && DP_IN(k, P.N)) {
+        lmax_next = k + 1 >= P.N ? P.n_t - 1 : sc.lmax[k + 1];
+        lmax_out = sc.lmax + k;
+    }
     bellman_tile<R, true, TILE_FULL, QLD>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
                                            sc.spl + row * P.n_u, sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn,
-                                           Vk, pik, i, blockIdx.x, smem_raw, sc.stats, 0, 0, nullptr, Qn, Qk);
+                                           Vk, pik, i, blockIdx.x, smem_raw, sc.stats, 0, 0, nullptr, Qn, Qk,
+                                           lmax_next, lmax_out, sc.lmax ? (int)gridDim.x : 0);
 }
 
 // Class-split tiles for grids whose tiles cannot fill the GPU: blockIdx.z

@@ -167,10 +167,10 @@ class EcoDP:
     def sweep_stats(self, stream=None):
         """Counters of the last sweep: effective state x control evaluations,
         state x class pairs, and the bytes of one update / one rollout copy."""
-        out = (C.c_int64 * 7)()
+        out = (C.c_int64 * 8)()
         N.check(N.dp_sweep_stats(self.h, out, _stream_handle(stream)), "dp_sweep_stats")
         return dict(effective_evals=out[0], class_evals=out[1], h2d_update_bytes=out[2], d2h_rollout_bytes=out[3],
-                    argmin_states=out[5], envelope_evals=out[6])
+                    argmin_states=out[5], envelope_evals=out[6], skipped_states=out[7])
 
     def value(self, k: int, stream=None) -> torch.Tensor:
         out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
