@@ -38,10 +38,10 @@ FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample e
 # dram__bytes_read.sum + dram__bytes_write.sum of one Bellman launch (stage 79
 # of this workload) from an ncu capture of the current kernel version (ncu's
 # counters cannot be read inside a timed run; ncu empties the caches before
-# the launch, so J_{k+1}'s corner quads, 12.5 MB, come from DRAM there, while
-# in the sweep the previous launch has just written them to L2).  None
-# whenever the kernel has changed since the last capture.
-BELLMAN_TRAFFIC_BYTES = 13.398528e6
+# the launch, so the corner quads of J_{k+1} that the launch reads come from
+# DRAM there, while in the sweep the previous launch has just written them to
+# L2).  None whenever the kernel has changed since the last capture.
+BELLMAN_TRAFFIC_BYTES = 11.023872e6
 
 
 def parse():
@@ -462,7 +462,8 @@ def bench_paper_grid(dev, stream, reps=20):
 
 
 ROOFLINE_KEYS = ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic", "peak_basis",
-                 "peak_measured", "frac_of_measured", "onchip_peaks_gbs", "bellman_ms_per_launch", "share_of_sweep")
+                 "peak_measured", "frac_of_measured", "onchip_peaks_gbs", "bellman_ms_per_launch", "share_of_sweep",
+                 "skipped_state_fraction")
 
 
 def headline(adjoint, paper_grid, batched, serving, c0=None):
@@ -572,6 +573,10 @@ def run_ours(args):
                 "envelope_evals_per_launch": stats["envelope_evals"] / p.n_stages,
                 "class_evals_per_launch": stats["class_evals"] / p.n_stages,
                 "envelope_fraction": stats["envelope_evals"] / max(1, stats["effective_evals"]),
+                # (state, stage) pairs past the next stage's last feasible
+                # time column: written infeasible without evaluation (the
+                # work counters above exclude them)
+                "skipped_state_fraction": stats["skipped_states"] / (p.n_stages * p.n_states),
                 "argmin_states": stats["argmin_states"],
                 # context: the direct trilinear form evaluates every state x
                 # control with 8 FMA (16 FLOP); at this kernel's time it would
