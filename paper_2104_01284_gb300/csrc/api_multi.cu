@@ -65,6 +65,7 @@ struct dp_multi {
     std::vector<cudaGraphExec_t> inst_graph;  // per instance, captured on first use
     std::vector<float4 *> quad;               // per instance: two slots, or null
     std::vector<size_t> quad_elems;
+    std::vector<int *> lmax;  // [B][N + 1] last feasible time column per stage (per-instance mode)
     std::vector<int> stream_of, launch_order;
     bool quads_ready = false;
 
@@ -217,12 +218,17 @@ dp_status enqueue_instance(dp_multi *m, int b, cudaStream_t s)
     float4 *q = m->quad[b];
     auto V = [&](int k) { return I.V + (size_t)k * I.stage_elems; };
     auto Q = [&](int k) { return q ? q + (size_t)(k & 1) * m->quad_elems[b] : nullptr; };
+    // the stages' last feasible time columns, as in a single-problem sweep
+    StageScratch sc = I.sc;
+    sc.lmax = b < (int)m->lmax.size() ? m->lmax[b] : nullptr;
+    if (sc.lmax)
+        DP_CUDA(cudaMemsetAsync(sc.lmax, 0xff, (size_t)(P.N + 1) * sizeof(int), s));
     DP_CUDA(launch_terminal(dP, P, V(P.N), s));
     if (q)
         DP_CUDA(launch_quad_from_pad(P, V(P.N), Q(P.N), s));
     DP_CUDA(launch_precompute(dP, P, I.tb, 0, P.N, I.sc, s));
     for (int k = P.N - 1; k >= 0; --k)
-        DP_CUDA(launch_bellman(dP, P, I.tb, k, I.sc, V(k + 1), V(k), I.pi + (size_t)k * I.pi_elems, 1, s, Q(k + 1),
+        DP_CUDA(launch_bellman(dP, P, I.tb, k, sc, V(k + 1), V(k), I.pi + (size_t)k * I.pi_elems, 1, s, Q(k + 1),
                                Q(k)));
     return DP_OK;
 }
@@ -238,8 +244,12 @@ dp_status set_streams(dp_multi *m, int K)
     if (!m->quads_ready) {
         m->quad.assign(m->B, nullptr);
         m->quad_elems.assign(m->B, 0);
+        m->lmax.assign(m->B, nullptr);
         for (int b = 0; b < m->B; ++b) {
             const DevParams &P = m->hP[b];
+            dp_status st_l = m_alloc_n(m, (size_t)P.N + 1, &m->lmax[b]);
+            if (st_l != DP_OK)
+                return st_l;
             const size_t e = (size_t)P.n_v * quad_rows(P.n_xi) * quad_ld(P.n_t);
             if (e == 0)
                 continue;
