@@ -132,6 +132,32 @@ def test_envelopes_keep_every_minimum(gpu, name):
         b.close()
 
 
+@pytest.mark.parametrize("name", ["paper_scale", "paper_grid_12_stages"])
+def test_skipped_states_are_exactly_those_past_the_last_feasible_time(gpu, name):
+    """The tiled sweep (grids whose tiles fill the GPU; the class-split launch
+    of smaller grids evaluates every state) writes infeasible, without
+    evaluating them, the states whose time lies past the last time column of
+    J_{k+1} holding a feasible value (every successor time is at least the
+    state's own).  From the solved values: every such state of J_k is
+    infeasible, and the sweep's counter of skipped states equals their
+    number, so the work counters the roofline uses exclude exactly them."""
+    p = P.config1(seed=1) if name == "paper_scale" else P.config1(seed=3, n_stages=12)
+    dp = gpu(p)
+    dp.solve()
+    st = dp.sweep_stats()
+    expected = 0
+    for k in range(p.n_stages):
+        cols = torch.isfinite(dp.value(k + 1)).any(dim=0).any(dim=0)
+        idx = torch.nonzero(cols).flatten()
+        first_skipped = int(idx.max()) + 1 if idx.numel() else 0
+        if first_skipped < p.n_t:
+            expected += p.n_v * p.n_soc * (p.n_t - first_skipped)
+            assert not torch.isfinite(dp.value(k)[:, :, first_skipped:]).any(), k
+    assert st["skipped_states"] == expected
+    assert expected > (0.3 * p.n_stages * p.n_states if name == "paper_scale" else 0)  # 45.7 % at paper scale
+    dp.close()
+
+
 @pytest.mark.parametrize("variant,n_t", [("tiled", 201), ("tiled6", 201), ("tiled", 101), ("tiled", 45),
                                          ("tiled", 62), ("tiled", 254)])
 def test_unsplit_tiled_sweep_bit_identical(gpu, variant, n_t):
