@@ -72,6 +72,7 @@ struct dp_problem {
     int *d_roll_u = nullptr;
     unsigned long long *d_stats = nullptr;
     int *d_lmax = nullptr;  // [N + 1] last feasible time column per stage of the last sweep
+    bool fill_slots = true;  // the sweep's tiles fill every resident CTA slot (a solve that runs alone)
     double *d_lam = nullptr;  // adjoint weights of two consecutive stages
     int *d_front = nullptr;   // adjoint support lists (AdjFrontier)
     unsigned *d_fbits = nullptr;
@@ -466,6 +467,7 @@ cudaError_t sweep_stage(dp_problem *p, int k, cudaStream_t s)
 {
     StageScratch sc = p->scratch();
     sc.lmax = p->d_lmax;  // J_{k+1}'s last feasible time column in, J_k's out
+    sc.fill_slots = p->fill_slots ? 1 : 0;
     return launch_bellman(p->dP, p->hP, p->tables(), k, sc, p->Vsweep(k + 1), p->Vsweep(k), p->pi(k), p->variant, s,
                           p->quad(k + 1), p->quad(k));
 }
@@ -502,6 +504,17 @@ dp_status enqueue_sweep(dp_problem *p, cudaStream_t s)
 
 namespace ecodp {
 namespace host {
+
+void set_fill_slots(dp_problem *p, bool on)
+{
+    if (p->fill_slots != on) {
+        p->fill_slots = on;
+        if (p->gexec)
+            cudaGraphExecDestroy(p->gexec);  // the captured launches hold the grid
+        p->gexec = nullptr;
+    }
+}
+
 
 size_t roll_doubles(int N) { return (size_t)(3 * (N + 1) + 3 * N + 4); }
 

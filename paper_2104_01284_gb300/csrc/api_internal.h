@@ -64,6 +64,9 @@ dp_status rollout_async(dp_problem *p, const double x0[3], double *h_out, int *h
 // Fill a caller's trajectory from a rollout record; returns its fail stage.
 int unpack_rollout(int N, const double *h, const int *hu, dp_trajectory *traj);
 size_t problem_bytes(const dp_problem *p);  // device bytes the problem holds
+// Whether p's sweeps fill every resident CTA slot (default: a solve that runs
+// alone) or keep one tile per 128 lanes (solves that share the GPU).
+void set_fill_slots(dp_problem *p, bool on);
 int problem_stages(const dp_problem *p);
 // Whether dp_problem_update can load d into p (same sizes and class structure).
 bool problem_fits(const dp_problem *p, const dp_problem_desc *d);

@@ -460,6 +460,7 @@ dp_status dp_multi_create(const dp_problem_desc *descs, int32_t n, const dp_mult
         I.sc.stats = nullptr;
         I.sc.part = nullptr;
         I.sc.lmax = nullptr;
+        I.sc.fill_slots = 0;  // the instances share the GPU
         m->out_off[b] = m->out_total;
         m->out_total += (long long)roll_doubles(P.N);
         m->u_off[b] = m->u_total;

@@ -201,6 +201,7 @@ dp_status dp_batch_submit(dp_batch_t b, const dp_problem_desc *desc, const doubl
         pick = victim;
     }
     dp_batch::Slot &S = b->slots[pick];
+    set_fill_slots(S.p, b->max_slots == 1);  // several slots share the GPU
     st = dp_solve_backward(S.p, (void *)S.s);
     if (st != DP_OK)
         return st;

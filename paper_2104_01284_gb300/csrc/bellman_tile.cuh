@@ -648,13 +648,14 @@ __device__ void bellman_tile(const DevParams &P, const StageTables &tb, int k, c
             n_tc = max(lmax_next + 1, 0);
     }
     const int n_act = n_jg * n_tc;  // lanes (SoC group, time column) of the row
-    // With fewer lanes, the classes of a lane group may be split over S warps
-    // (contiguous class slices, merged in class order after the loop) as long
-    // as the row's lanes stay within its n_chunks tiles: a warp's class loop
-    // is a chain of dependent instructions, and S warps finish it sooner.
+    // Where the row's n_chunks tiles (the launch fills every resident CTA
+    // slot) hold more lanes than the row needs, the classes of a lane group
+    // are split over S warps (contiguous class slices, merged in class order
+    // after the loop): a warp's class loop is a chain of dependent
+    // instructions, and S warps finish it sooner.
     int S = 1;
     if constexpr (MODE == TILE_FULL && NC) {
-        if (n_tc < P.n_t) {
+        if (n_chunks > 0) {
             if ((4 * n_act + TLANES - 1) / TLANES <= n_chunks)
                 S = 4;
             else if ((2 * n_act + TLANES - 1) / TLANES <= n_chunks)

@@ -319,6 +319,10 @@ struct StageScratch {
     // feasible state (-1: none; all -1 before the sweep, J_N's is n_t - 1
     // without an entry).  NULL: the launch neither reads nor writes it.
     int *lmax;
+    // 1: a sweep that runs alone; its tiles fill every resident CTA slot
+    // (the spare ones take class slices).  0: solves that share the GPU keep
+    // one tile per 128 lanes.
+    int fill_slots;
 };
 
 // One instance of a batch (device-resident descriptor).

@@ -8,6 +8,8 @@
 #include <cfloat>
 #include <climits>
 
+#include <algorithm>
+
 #include "bellman_tile.cuh"
 
 #undef ECODP_FILE_TAG
@@ -186,9 +188,7 @@ __global__ void __launch_bounds__(256) bellman_join(const DevParams *__restrict_
         atomicAdd(sc.stats + 3, (unsigned long long)n_find);
 }
 
-// Class slices per tile: as many as keep the GPU's resident CTA slots (4 per
-// SM) filled, at most 8; 1 (no split) when the tiles alone fill the slots.
-int class_slices(int tiles)
+int sm_count()
 {
     static int sms = 0;
     if (sms == 0) {
@@ -197,7 +197,14 @@ int class_slices(int tiles)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             sms = 1;
     }
-    const int s = (4 * sms) / (tiles > 0 ? tiles : 1);
+    return sms;
+}
+
+// Class slices per tile: as many as keep the GPU's resident CTA slots (4 per
+// SM) filled, at most 8; 1 (no split) when the tiles alone fill the slots.
+int class_slices(int tiles)
+{
+    const int s = (4 * sm_count()) / (tiles > 0 ? tiles : 1);
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
 
@@ -243,7 +250,11 @@ cudaError_t launch_tiles(const DevParams *dP, const DevParams &hP, StageTables t
         cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return err;
-        kernel<<<dim3(chunks, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
+        // in a sweep the tiles of a row fill every resident CTA slot: those
+        // beyond the row's lanes take class slices (bellman_tile)
+        const int grid_x =
+            sc.lmax && sc.fill_slots ? std::max(chunks, tile_minb<R>() * sm_count() / hP.n_v) : chunks;
+        kernel<<<dim3(grid_x, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
         return cudaGetLastError();
     };
     switch (qld) {
