@@ -118,6 +118,110 @@ __global__ void __launch_bounds__(TLANES, tile_minb<R>())
                                            lmax_next, lmax_out, sc.lmax ? (int)gridDim.x : 0);
 }
 
+// Row plan of a sweep stage that runs alone (every CTA computes the same):
+// speed row r's class table costs 24 per class plus its lines (the tile's
+// work per lane), and takes c1, c2 or c4 tiles (its lanes at 1, 2 or 4 class
+// slices per lane group) for the least target cost tau such that the rows
+// with cost <= tau take c1, <= 2 tau c2, the rest c4, and all tiles fit in
+// the launch's G CTAs; so the rows that cost most split their classes first.
+// CTA b takes the row whose tiles, in row order, hold b: out = {row, tile of
+// the row, tiles of the row}, row -1 for a CTA beyond them.  Warp 0 only.
+constexpr int PLAN_ROWS_PER_LANE = 8;  // up to 256 speed rows
+
+__device__ void plan_tile(const DevParams &P, const StageScratch &sc, int k, int n_act, int b, int G, int *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int c1 = max((n_act + TLANES - 1) / TLANES, 1);
+    const int c2 = max((2 * n_act + TLANES - 1) / TLANES, 1);
+    const int c4 = max((4 * n_act + TLANES - 1) / TLANES, 1);
+    int cost[PLAN_ROWS_PER_LANE];
+    int cmax = 0;
+#pragma unroll
+    for (int q = 0; q < PLAN_ROWS_PER_LANE; ++q) {
+        const int r = lane + 32 * q;
+        cost[q] = -1;
+        if (r < P.n_v) {
+            const size_t row = (size_t)k * P.n_v + r;
+            cost[q] = 24 * max(sc.row_cnt[2 * row], 0) + max(sc.row_cnt[2 * row + 1], 0);
+            cmax = max(cmax, cost[q]);
+        }
+    }
+    cmax = __reduce_max_sync(0xffffffffu, cmax);
+    auto tiles = [&](int c, int tau) { return c < 0 ? 0 : (c <= tau ? c1 : (c <= 2 * tau ? c2 : c4)); };
+    int lo = 0, hi = cmax;  // at tau = cmax every row takes c1, which fits (the host checks)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        int n = 0;
+#pragma unroll
+        for (int q = 0; q < PLAN_ROWS_PER_LANE; ++q)
+            n += tiles(cost[q], mid);
+        if (__reduce_add_sync(0xffffffffu, n) <= G)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    int base = 0, f_row = -1, f_tile = 0, f_n = 0;
+#pragma unroll
+    for (int q = 0; q < PLAN_ROWS_PER_LANE; ++q) {
+        const int c = tiles(cost[q], lo);
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d)
+                incl += y;
+        }
+        const int start = base + incl - c;
+        if (c > 0 && b >= start && b < start + c) {
+            f_row = lane + 32 * q;
+            f_tile = b - start;
+            f_n = c;
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, f_row >= 0);
+    const int src = m ? __ffs((int)m) - 1 : 0;
+    const int row = __shfl_sync(0xffffffffu, f_row, src), tile = __shfl_sync(0xffffffffu, f_tile, src),
+              n = __shfl_sync(0xffffffffu, f_n, src);
+    if (lane == 0) {
+        out[0] = m ? row : -1;
+        out[1] = tile;
+        out[2] = n;
+    }
+}
+
+// A sweep stage that runs alone, its tiles placed by the row plan above on a
+// 1-D grid of every resident CTA slot.
+template <int R, int QLD>
+__global__ void __launch_bounds__(TLANES, tile_minb<R>())
+    bellman_planned(const DevParams *__restrict__ dP, StageTables tb, int k, StageScratch sc,
+                    const float *__restrict__ Vn, float *__restrict__ Vk, int16_t *__restrict__ pik,
+                    const float4 *__restrict__ Qn, float4 *__restrict__ Qk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ DevParams P;
+    __shared__ int s_plan[3];
+    if (threadIdx.x == 0)
+        P = *dP;
+    __syncthreads();
+    if (!DP_IN(k, P.N) || !sc.lmax)
+        return;
+    const int lmax_next = k + 1 >= P.N ? P.n_t - 1 : sc.lmax[k + 1];
+    const int n_tc = lmax_next >= P.n_t - 1 ? P.n_t : max(lmax_next + 1, 0);  // as bellman_tile
+    const int n_act = (P.n_xi + R - 1) / R * n_tc;
+    if (threadIdx.x < 32)
+        plan_tile(P, sc, k, n_act, (int)blockIdx.x, (int)gridDim.x, s_plan);
+    __syncthreads();
+    const int i = s_plan[0];
+    if (i < 0 || i >= P.n_v || s_plan[2] < 1)
+        return;  // a spare slot (uniform over the CTA)
+    const size_t row = (size_t)k * P.n_v + i;
+    bellman_tile<R, true, TILE_FULL, QLD>(P, tb, k, sc.cls + row * P.n_cls, sc.ent + row * P.n_cls,
+                                           sc.spl + row * P.n_u, sc.row_cnt[2 * row], sc.row_cnt[2 * row + 1], Vn,
+                                           Vk, pik, i, s_plan[1], smem_raw, sc.stats, 0, 0, nullptr, Qn, Qk,
+                                           lmax_next, sc.lmax + k, s_plan[2]);
+}
+
 // Class-split tiles for grids whose tiles cannot fill the GPU: blockIdx.z
 // picks one of gridDim.z slices of the row's class list (TILE_SLICE in
 // bellman_tile.cuh); a per-state join launch then writes J_k and the argmin.
@@ -246,26 +350,37 @@ cudaError_t launch_tiles(const DevParams *dP, const DevParams &hP, StageTables t
         return cudaGetLastError();
     }
     const int qld = Qn && Qk ? quad_ld(hP.n_t) : 0;
-    auto run = [&](auto kernel) {
+    // a sweep that runs alone fills every resident CTA slot with tiles: by
+    // the row plan where the rows fit one tile per 128 lanes, else with the
+    // same number of tiles per row (tiles beyond a row's lanes take class
+    // slices, bellman_tile)
+    const int slots = tile_minb<R>() * sm_count();
+    const bool planned = sc.lmax && sc.fill_slots && hP.n_v <= 32 * PLAN_ROWS_PER_LANE && hP.n_v * chunks <= slots;
+    auto run = [&](auto kernel, auto planned_kernel) {
+        if (planned) {
+            cudaError_t err =
+                cudaFuncSetAttribute(planned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess)
+                return err;
+            planned_kernel<<<slots, TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
+            return cudaGetLastError();
+        }
         cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return err;
-        // in a sweep the tiles of a row fill every resident CTA slot: those
-        // beyond the row's lanes take class slices (bellman_tile)
-        const int grid_x =
-            sc.lmax && sc.fill_slots ? std::max(chunks, tile_minb<R>() * sm_count() / hP.n_v) : chunks;
+        const int grid_x = sc.lmax && sc.fill_slots ? std::max(chunks, slots / hP.n_v) : chunks;
         kernel<<<dim3(grid_x, hP.n_v), TLANES, smem, s>>>(dP, tb, k, sc, Vnext, Vk, pik, Qn, Qk);
         return cudaGetLastError();
     };
     switch (qld) {
     case 64:
-        return run(bellman_tiled<R, 64>);
+        return run(bellman_tiled<R, 64>, bellman_planned<R, 64>);
     case 128:
-        return run(bellman_tiled<R, 128>);
+        return run(bellman_tiled<R, 128>, bellman_planned<R, 128>);
     case 256:
-        return run(bellman_tiled<R, 256>);
+        return run(bellman_tiled<R, 256>, bellman_planned<R, 256>);
     default:
-        return run(bellman_tiled<R, 0>);
+        return run(bellman_tiled<R, 0>, bellman_planned<R, 0>);
     }
 }
 
