@@ -41,7 +41,7 @@ FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample e
 # the launch, so the corner quads of J_{k+1} that the launch reads come from
 # DRAM there, while in the sweep the previous launch has just written them to
 # L2).  None whenever the kernel has changed since the last capture.
-BELLMAN_TRAFFIC_BYTES = 11.023872e6
+BELLMAN_TRAFFIC_BYTES = 10.957312e6
 
 
 def parse():
@@ -560,7 +560,7 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks.get("sm_mhz") or FALLBACK_SM_MHZ
     peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "bellman_tiled", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "kernel": "bellman_planned", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": BELLMAN_TRAFFIC_BYTES,
                 "peak_basis": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {mhz:.0f} MHz "
