@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(TLANES, tile_minb<R>())
 }
 
 // Row plan of a sweep stage that runs alone (every CTA computes the same):
-// speed row r's class table costs 24 per class plus its lines (the tile's
-// work per lane), and takes c1, c2 or c4 tiles (its lanes at 1, 2 or 4 class
+// speed row r's class table costs 12 per class plus its lines (class_cost in
+// bellman_tile.cuh), and takes c1, c2 or c4 tiles (its lanes at 1, 2 or 4 class
 // slices per lane group) for the least target cost tau such that the rows
 // with cost <= tau take c1, <= 2 tau c2, the rest c4, and all tiles fit in
 // the launch's G CTAs; so the rows that cost most split their classes first.
@@ -142,7 +142,7 @@ __device__ void plan_tile(const DevParams &P, const StageScratch &sc, int k, int
         cost[q] = -1;
         if (r < P.n_v) {
             const size_t row = (size_t)k * P.n_v + r;
-            cost[q] = 24 * max(sc.row_cnt[2 * row], 0) + max(sc.row_cnt[2 * row + 1], 0);
+            cost[q] = 12 * max(sc.row_cnt[2 * row], 0) + max(sc.row_cnt[2 * row + 1], 0);
             cmax = max(cmax, cost[q]);
         }
     }
