@@ -41,7 +41,7 @@ FALLBACK_SM_MHZ = 2070.0  # maximum SM clock of the part, when no clock sample e
 # the launch, so the corner quads of J_{k+1} that the launch reads come from
 # DRAM there, while in the sweep the previous launch has just written them to
 # L2).  None whenever the kernel has changed since the last capture.
-BELLMAN_TRAFFIC_BYTES = 10.957312e6
+BELLMAN_TRAFFIC_BYTES = 10.954752e6
 
 
 def parse():
