@@ -152,8 +152,9 @@ dp_status dp_problem_destroy(dp_problem_t p);
  * (the FP32 minimum is that of all controls, see dp_set_envelopes).  Successor
  * times never precede the state's own time, so a state whose time node lies
  * beyond the last time column of J_{k+1} holding a feasible value reads only
- * infeasible values: the tiled kernel writes such states infeasible without
- * evaluating them, warp by warp (the result is the same).  Exact FP32 ties
+ * infeasible values: the sweep writes such states infeasible without
+ * evaluating them, and the GPU threads that frees share the class lists of
+ * the remaining states (the results are the same).  Exact FP32 ties
  * are broken in the order (torque class, control index): the first class,
  * ordered by brake flag and then by ascending total torque, that reaches the
  * minimum, then the lowest control index inside that class.  Asynchronous on stream;
